@@ -1,0 +1,359 @@
+"""Benchmark: blocked Floyd-Warshall APSP on one GB300 (and N independent replicas).
+
+Default workload (one "step" = one full all-pairs shortest-paths solve, all
+three phases of every block round, through the library's C ABI):
+  dense random digraph, n = 32768, fp32 integer weights uniform in [1, 1000],
+  zero diagonal, int32 path matrix -- 4 GiB D + 4 GiB P, far larger than L2,
+  so no cache flush is needed between steps.
+Metric: APSP GFLOPS = 2 n^3 / step time (the 2n^3 convention: one add and one
+compare per relaxation, n^3 relaxations).
+
+Printed JSON line (rank 0): value (device-timed, inputs resident in HBM),
+e2e (same metric through apsp_fw_host with host buffers, copies included),
+roofline of the dominant kernel (phase 3, bound by the ALU pipe that
+executes FMNMX), cpu_baseline (the serial oracle on a bounded sample), clocks
+sampled during the timed region, and the 16-bit path on the n = 32768,
+weights in [1, 2] workload as an extra key.
+
+`--impl reference` times the serial C oracle instead (this repository has no
+other reference implementation), on a bounded sample per step.
+
+Multi-GPU: every graph is independent, so N ranks run N independent replicas
+("replicas only", weak scaling; no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Roofline denominators (unit counts x clock): 152 SMs; the FP32 min (FMNMX)
+# issues at 64 lanes/clk/SM on the ALU pipe, one per relaxation, so the fp32
+# update peak is 152 * 64 * f updates/s = 2 * 152 * 64 * f "flops"/s in the 2n^3
+# convention; the packed 16-bit path (min.u16x2: 2 mins per lane) doubles it.
+SMS = 152
+SM_MAX_MHZ = 2070.0
+ALU_PEAK_F32_TFLOPS = 2 * SMS * 64 * SM_MAX_MHZ * 1e6 / 1e12      # 40.27
+ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
+
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "phase3_f32_n32768_bs64.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1811_01201_gb300", "csrc", "fw_minplus_f32.cuh")
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows: list[list[str]] = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self) -> dict:
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile():
+    """Per-launch DRAM bytes of the phase-3 kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel source changed since."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    got = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            got[k.strip()] = v.strip().strip("`")
+    if got.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(got["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+
+def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: int):
+    import oracle
+    from paper_1811_01201_gb300 import inputs
+    W = inputs.dense_digraph(n_full, seed, lo, hi, rows=(0, n_sample))[:, :n_sample].contiguous().numpy()
+    t0 = time.perf_counter()
+    oracle.fw_blocked(W, bs)
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * n_sample ** 3
+
+
+def cpu_baseline(args) -> dict:
+    dt, flops = _oracle_sample(args.n, args.seed, 1, 1000, args.cpu_sample_n, args.bs)
+    return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
+            "sample": f"serial C blocked FW (BS={args.bs}) on the leading {args.cpu_sample_n}x{args.cpu_sample_n} "
+                      f"block of the n={args.n} workload, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs)
+    times = []
+    flops = 0.0
+    for _ in range(args.steps):
+        dt, fl = _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs)
+        times.append(dt)
+        flops = fl
+    tot = sum(times)
+    val = flops * args.steps / tot / 1e9
+    line = {"impl": "reference", "metric": "APSP GFLOPS (2n^3/s)", "value": round(val, 4), "unit": "GFLOPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(args),
+            "cpu_baseline": {"value": round(val, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
+                             "sample": f"serial C blocked FW (BS={args.bs}) on the leading "
+                                       f"{args.ref_sample_n}x{args.ref_sample_n} block of the n={args.n} workload "
+                                       "per step"},
+            "e2e": {"value": round(val, 4), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(args) -> dict:
+    return {"workload": f"dense random digraph n={args.n}, fp32 integer weights U[1,1000], zero diagonal, "
+                        "int32 path matrix (blocked Floyd-Warshall, one full solve per step)",
+            "n": args.n, "bs": args.bs, "weights": "int [1,1000]", "density": 1.0,
+            "l2": "inputs larger than L2 (4 GiB D + 4 GiB P at n=32768); no flush"}
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    apsp.load(build_if_missing=True)
+    n = args.n
+    s = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    W = inputs.dense_digraph(n, args.seed, 1, 1000, device=dev)
+    D = torch.empty_like(W)
+    P = torch.empty((n, n), dtype=torch.int32, device=dev)
+    ws = torch.empty(apsp.apsp_fw_workspace_size(n, bs=args.bs, dtype=apsp.DTYPE_F32), dtype=torch.uint8,
+                     device=dev)
+
+    def step(flags=0):
+        return apsp.apsp_fw_ex(W, D, P, bs=args.bs, dtype=apsp.DTYPE_F32, validate=True, workspace=ws,
+                               flags=flags)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # Timed region: K steps bracketed by barrier + synchronize; phase-3 launches
+    # timed with CUDA events on the launching stream inside the library.
+    ph_ms = [0.0, 0.0, 0.0]
+    ph_launch = [0, 0, 0]
+    launches = 0
+    info = None
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            info = step(flags=apsp.FLAG_TIME_PHASES)
+            for q in range(3):
+                ph_ms[q] += info.phase_ms[q]
+                ph_launch[q] += info.phase_launches[q]
+            launches += info.launches
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = 2.0 * n ** 3
+    value = flops * args.steps * world / (ms * 1e-3) / 1e9
+
+    # Phase-3 roofline: algorithmic relaxations of all phase-3 launches
+    # ((n - BS)^2 * BS per round, 2 flops each) / their summed event time.
+    R = n // args.bs
+    ph3_flops = 2.0 * (n - args.bs) ** 2 * args.bs * (R) * args.steps
+    ph3_tflops = ph3_flops / (ph_ms[2] * 1e-3) / 1e12 if ph_ms[2] > 0 else None
+    roof = {"bound": "alu", "achieved": round(ph3_tflops, 3) if ph3_tflops else None,
+            "peak": round(ALU_PEAK_F32_TFLOPS, 2), "unit": "TFLOP/s",
+            "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
+            "traffic": _traffic_from_profile(),
+            "kernel": f"fw_phase3_f32_kernel<{args.bs}>",
+            "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
+            "phase_ms_per_step": [round(x / args.steps, 3) for x in ph_ms],
+            "phase_launches_per_step": [x // args.steps for x in ph_launch]}
+    clocks = clk.summary()
+
+    line = {"metric": "APSP GFLOPS (2n^3/s)", "value": round(value, 2), "unit": "GFLOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(args) | {"parallelism": f"replicas x{world}"},
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks}
+
+    # 16-bit exact path on its workload (n, weights in [1,2]: max_w*(n-1) < 65535).
+    if args.u16:
+        Wu = inputs.dense_digraph(n, args.seed + 2, 1, 2, device=dev)
+        wsu = torch.empty(apsp.apsp_fw_workspace_size(n, bs=args.bs), dtype=torch.uint8, device=dev)
+        for _ in range(max(1, args.warmup - 1)):
+            apsp.apsp_fw_ex(Wu, D, P, bs=args.bs, workspace=wsu)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s)
+        for _ in range(args.steps):
+            iu = apsp.apsp_fw_ex(Wu, D, P, bs=args.bs, workspace=wsu)
+        a1.record(s)
+        torch.cuda.synchronize()
+        ums = a0.elapsed_time(a1) / args.steps
+        line["u16x2"] = {"workload": f"dense digraph n={n}, integer weights U[1,2] (16-bit eligible)",
+                         "value": round(flops / (ums * 1e-3) / 1e9, 2), "unit": "GFLOPS",
+                         "ms_per_step": round(ums, 3), "dtype_used": "u16x2" if iu.dtype_used == 2 else "f32",
+                         "peak_tflops": round(ALU_PEAK_U16_TFLOPS, 2)}
+        del Wu, wsu
+
+    # End to end through apsp_fw_host: host pinned W in, host D and P out, every step.
+    if args.e2e:
+        Wh = W.cpu().pin_memory()
+        Dh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        Ph = torch.empty((n, n), dtype=torch.int32).pin_memory()
+        del W, D, P, ws
+        torch.cuda.empty_cache()
+        apsp.apsp_fw_host(Wh, Dh, Ph, bs=args.bs, dtype=apsp.DTYPE_F32)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            apsp.apsp_fw_host(Wh, Dh, Ph, bs=args.bs, dtype=apsp.DTYPE_F32)
+        torch.cuda.synchronize()
+        barrier()
+        et = (time.perf_counter() - t0) / args.e2e_steps
+        line["e2e"] = {"value": round(flops * world / et / 1e9, 2), "unit": "GFLOPS",
+                       "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": 8 * n * n,
+                       "ms_per_step": round(et * 1e3, 3), "steps": args.e2e_steps,
+                       "api": "apsp_fw_host (pinned host buffers)"}
+
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--bs", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--no-u16", dest="u16", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-sample-n", type=int, default=1280)
+    ap.add_argument("--ref-sample-n", type=int, default=768)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "gb300":
+            import torch
+            torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

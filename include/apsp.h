@@ -1,0 +1,233 @@
+/*
+ * apsp.h -- C ABI of the GB300 blocked Floyd-Warshall library (libapsp.so).
+ *
+ * The method is the blocked all-pairs shortest-paths algorithm studied in
+ * Rucci, De Giusti, Naiouf, "Blocked All-Pairs Shortest Paths Algorithm on
+ * Intel Xeon Phi KNL Processor: A Case Study" (arXiv 1811.01201):
+ *   - problem statement (Section 3): input an N x N distance matrix D with
+ *     D[i][j] the weight of edge i -> j; output D[i][j] = shortest distance and
+ *     P[i][j] = the most recently added intermediate vertex, for path
+ *     reconstruction;
+ *   - blocking (Section 4.1, Fig. 2-3): D split into BS x BS blocks, R = N/BS
+ *     rounds, each round updating the diagonal block, then the blocks of its
+ *     row and column, then all remaining blocks;
+ *   - relaxation (Section 4.2): one addition and one comparison per update,
+ *     here a strict '<', so ties keep the earlier intermediate.
+ *
+ * Conventions shared by every call:
+ *   - Matrices are dense, row-major, n x n, leading dimension n, 4-byte
+ *     elements: weights/distances are IEEE fp32, path entries int32.
+ *   - Absent edges are +INFINITY. Weights must be >= 0 (or +INF) and not NaN;
+ *     W[i][i] is ignored (the diagonal of D is forced to 0).
+ *   - P[i][j] = -1 means "direct edge, i == j, or unreachable"; otherwise it is
+ *     the global index of the intermediate vertex recorded by the last strict
+ *     improvement of D[i][j]. The path is path(i,P[i][j]) ++ path(P[i][j],j).
+ *   - Device pointers are CUDA global-memory pointers owned by the caller;
+ *     `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is enqueued on `stream`; the call returns once it is
+ *     enqueued, except where a call says it synchronises.
+ *   - No call aborts the process. Every call returns an apsp_status; a sticky
+ *     CUDA error is reported as APSP_ECUDA.
+ *   - Results are deterministic: for the same W, n and block size they are
+ *     bit-identical from run to run and between the single-graph, batched and
+ *     served entry points.
+ */
+#ifndef APSP_H
+#define APSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APSP_OK = 0,
+  APSP_EINVAL = -1,     /* bad argument: n < 1, NULL pointer, negative or NaN weight, unsupported option */
+  APSP_ENOMEM = -2,     /* device/host allocation failed, workspace too small, or over the HBM budget */
+  APSP_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  APSP_ETIMEOUT = -4,   /* a bounded wait ran out (poll timeout, device-side spin limit) */
+  APSP_EBUSY = -5,      /* resource busy: no free slot, or the result is not ready yet */
+  APSP_ECANCELLED = -6, /* the job was cancelled or the server is shutting down */
+  APSP_ENOTFOUND = -7   /* unknown job id */
+} apsp_status;
+
+/* Arithmetic used for the distance matrix. */
+enum {
+  APSP_DTYPE_AUTO = 0,  /* U16X2 when eligible (see below), else F32 */
+  APSP_DTYPE_F32 = 1,   /* fp32 distances */
+  APSP_DTYPE_U16X2 = 2  /* exact packed 16-bit distances, two per 32-bit lane, saturating at 65535 = INF */
+};
+
+/*
+ * Per-call options. Zero-initialise and set what you need.
+ *   bs:       block size BS (Section 4.1). 0 = the library default for n
+ *             (apsp_default_bs); else 32, 64 or 128.
+ *   dtype:    APSP_DTYPE_*. U16X2 is eligible only when every finite weight is
+ *             an integer and max_w * (n - 1) < 65535, so that every path length
+ *             fits in 16 bits; it gives bit-identical D and P to F32.
+ *             Requesting U16X2 for an ineligible W returns APSP_EINVAL.
+ *   validate: 1 = scan W on the device for negative / NaN weights (and, for
+ *             AUTO/U16X2, eligibility) before running; the call then
+ *             synchronises `stream` once. 0 = trust the caller (F32 only;
+ *             fully asynchronous, usable inside CUDA-graph capture).
+ */
+typedef struct {
+  int bs;
+  int dtype;
+  int validate;
+  int flags;       /* APSP_FLAG_* bits */
+} apsp_options;
+
+/* APSP_FLAG_TIME_PHASES: record CUDA events around every phase launch and
+ * report the summed device time per phase in apsp_run_info.phase_ms; the call
+ * then synchronises `stream` before returning. */
+#define APSP_FLAG_TIME_PHASES 1
+
+/* What a call actually did (optional output). */
+typedef struct {
+  int bs_used;       /* block size of the run; the oracle must use the same BS to match P bit-exactly */
+  int dtype_used;    /* APSP_DTYPE_F32 or APSP_DTYPE_U16X2 */
+  int rounds;        /* number of block rounds R = n_pad / BS */
+  int n_pad;         /* working order: n rounded up to a multiple of 128 */
+  int launches;      /* kernels this call launched */
+  int phase_launches[3];
+  float phase_ms[3]; /* with APSP_FLAG_TIME_PHASES: device ms in phases 1, 2, 3 (else 0) */
+} apsp_run_info;
+
+/* Library default block size for order n (deterministic in n). */
+int apsp_default_bs(int n);
+
+/* Human-readable name of a status code (static string). */
+const char* apsp_status_str(apsp_status s);
+
+/*
+ * Bytes of device workspace apsp_fw_ex needs for (n, opt): always at least
+ * 256 (the input scan's counters); n*n-sized working matrices are added when
+ * n is not a multiple of 128 or the 16-bit path may be chosen. Returns 0 on
+ * invalid arguments (apsp_fw_ex reports them).
+ */
+size_t apsp_fw_workspace_size(int n, const apsp_options* opt);
+
+/*
+ * All-pairs shortest paths of one graph (Section 3; blocked per Section 4.1).
+ *   W: device, n*n fp32 weights (may alias D: in-place run).
+ *   D: device, n*n fp32 output distances.
+ *   P: device, n*n int32 output path matrix.
+ * Uses default options (bs = apsp_default_bs(n), dtype AUTO, validate 1), so
+ * it synchronises `stream` once after the validation scan. Any workspace is
+ * taken from the stream-ordered allocator and returned before the call ends.
+ */
+apsp_status apsp_fw(const float* W, float* D, int32_t* P, int n, void* stream);
+
+/*
+ * As apsp_fw with explicit options and caller-provided workspace.
+ *   opt: NULL = defaults.
+ *   workspace / workspace_bytes: device buffer of at least
+ *     apsp_fw_workspace_size(n, opt) bytes, 256-byte aligned, or NULL/0 to let
+ *     the library allocate with cudaMallocAsync on `stream`.
+ *   info: optional output (may be NULL).
+ */
+apsp_status apsp_fw_ex(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
+                       size_t workspace_bytes, apsp_run_info* info, void* stream);
+
+/*
+ * End-to-end call on HOST buffers: copies W (host, n*n fp32) to the device,
+ * runs apsp_fw_ex, copies D and P back to host memory, and synchronises
+ * `stream` before returning. W, D, P are host pointers (page-locked memory
+ * gives the fastest copies). Device memory is allocated and freed inside.
+ */
+apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
+                         apsp_run_info* info, void* stream);
+
+/*
+ * Many independent graphs in one persistent launch (one CTA works on one
+ * graph at a time; graphs are taken largest first from a device work queue).
+ *   W, D, P: HOST arrays of `count` DEVICE pointers; graph g has order n[g]
+ *            (host array), 1 <= n[g] <= APSP_BATCH_MAX_N, row-major with
+ *            leading dimension n[g]. W[g] may alias D[g].
+ *   opt:     bs must be 0 (per-graph default) or 32; dtype F32 or AUTO (the
+ *            batched kernel computes in fp32); validate as above.
+ *   bs_used: optional HOST array of `count` ints receiving each graph's BS.
+ * The call copies a descriptor table to the device through the stream and
+ * synchronises `stream` before returning (the table's staging memory is then
+ * released). Results equal apsp_fw_ex with bs = bs_used[g], bit for bit.
+ */
+#define APSP_BATCH_MAX_N 4096
+apsp_status apsp_fw_batched(const float* const* W, float* const* D, int32_t* const* P, const int* n, int count,
+                            const apsp_options* opt, int* bs_used, void* stream);
+
+/* Block size the batched kernel uses for a graph of order n. */
+int apsp_batched_bs(int n);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct apsp_server apsp_server;
+
+typedef struct {
+  uint64_t submitted;   /* jobs accepted by apsp_serve_submit */
+  uint64_t completed;   /* jobs whose results are ready */
+  uint64_t rejected;    /* submits refused (invalid, over budget) */
+  uint64_t in_flight;   /* admitted jobs not yet completed */
+  uint64_t queued;      /* submitted jobs waiting for admission */
+  double graphs_per_s;  /* completed / (time of last completion - time of first submit) */
+  double p50_ms;        /* median submit -> result-ready latency of completed jobs */
+  double p99_ms;        /* 99th percentile of the same */
+  double mean_ms;
+  double max_ms;
+  uint64_t hbm_in_use;  /* bytes of device memory held by admitted jobs */
+  uint64_t hbm_peak;    /* high-water mark of hbm_in_use */
+} apsp_stats;
+
+/*
+ * Create a continuous-batching server on the current CUDA device.
+ *   hbm_budget_bytes: cap on the device memory admitted jobs may hold at once
+ *                     (each job holds its D, P and staging buffers).
+ *   max_slots:        cap on jobs resident on the device at once (>= 1).
+ * A scheduler thread admits queued jobs as budget and slots free up, packs
+ * small graphs into batched launches and gives large graphs their own
+ * streams, so work submitted while other work runs overlaps on the device.
+ */
+apsp_status apsp_serve_create(apsp_server** out, size_t hbm_budget_bytes, int max_slots);
+
+/*
+ * Queue one APSP job. W is a HOST pointer to n*n fp32 weights; it is copied
+ * before the call returns. Never blocks on the GPU. *job_id receives the id.
+ * Returns APSP_EINVAL for a malformed W (negative / NaN weight, n < 1) and
+ * APSP_ENOMEM when the job alone could never fit in the HBM budget.
+ */
+apsp_status apsp_serve_submit(apsp_server* s, const float* W, int n, uint64_t* job_id);
+
+/*
+ * Wait up to timeout_ms (0 = don't wait, < 0 = forever) for job_id and copy
+ * its result to HOST buffers D (n*n fp32) and P (n*n int32); either may be
+ * NULL. On success the job is released. Returns APSP_EBUSY / APSP_ETIMEOUT
+ * while it is not ready, APSP_ENOTFOUND for an unknown id. bs_used (may be
+ * NULL) receives the block size the job ran with.
+ */
+apsp_status apsp_serve_poll(apsp_server* s, uint64_t job_id, float* D, int32_t* P, int* bs_used, int timeout_ms);
+
+/* Snapshot of the server's counters and latency percentiles. */
+apsp_status apsp_serve_stats(apsp_server* s, apsp_stats* out);
+
+/* Cancel queued jobs, drain the device, join the scheduler, free everything. */
+apsp_status apsp_serve_destroy(apsp_server* s);
+
+/* ---------------------------------------------------------------- host helpers */
+
+/*
+ * Vertices of the shortest path i -> j encoded in a HOST copy of P (n*n int32):
+ * writes i, ..., j into out (capacity cap) and returns the count, or -1 when
+ * the walk is malformed, exceeds cap or n vertices, or an index is out of range.
+ * Unreachable pairs (and i == j) give the single vertex i (count 1) only when
+ * i == j; for i != j with P == -1 the result is the direct edge (count 2) --
+ * check D[i][j] for reachability.
+ */
+int apsp_path(const int32_t* P, int n, int i, int j, int32_t* out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APSP_H */

@@ -1,0 +1,365 @@
+// Single-graph blocked Floyd-Warshall: host driver and C ABI (include/apsp.h).
+//
+// Per call: validate, pick the arithmetic (fp32, or exact 16-bit when every
+// path length fits), lay D/P out in a working layout whose order is a multiple
+// of 128, then run R = n_pad/BS block rounds (Section 4.1 of arXiv 1811.01201),
+// each as three stream-ordered launches: phase 1 (diagonal block), phase 2
+// (its row and column blocks), phase 3 (all remaining blocks). Kernel
+// boundaries are the barriers between the phases.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/apsp.h"
+#include "apsp_internal.h"
+#include "fw_aux.cuh"
+#include "fw_minplus_f32.cuh"
+#include "fw_minplus_u16.cuh"
+#include "fw_seq.cuh"
+
+namespace apsp {
+
+static int g_sm_count = 0;
+
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      g_sm_count = v;
+    else
+      g_sm_count = 152;
+  }
+  return g_sm_count;
+}
+
+static int elementwise_grid(size_t work) {
+  const size_t per = 256;
+  size_t g = (work + per - 1) / per;
+  return (int)std::max<size_t>(1, std::min<size_t>(g, (size_t)sm_count() * 16));
+}
+
+// ---------------------------------------------------------------- phase timing
+
+// Optional per-phase device timing (APSP_FLAG_TIME_PHASES): an event after
+// every phase launch; interval i is charged to the phase that ended it.
+struct PhaseTimer {
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> tag;
+  int launches[3] = {0, 0, 0};
+  bool on = false;
+  void mark(int phase) {
+    if (phase >= 0) ++launches[phase];
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    tag.push_back(phase);
+  }
+  void finish(float ms[3]) {
+    ms[0] = ms[1] = ms[2] = 0.f;
+    if (on && !ev.empty()) {
+      cudaEventSynchronize(ev.back());
+      for (size_t i = 1; i < ev.size(); ++i) {
+        float t = 0.f;
+        if (tag[i] >= 0 && cudaEventElapsedTime(&t, ev[i - 1], ev[i]) == cudaSuccess) ms[tag[i]] += t;
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    tag.clear();
+  }
+};
+
+// ---------------------------------------------------------------- launch tables
+
+template <class T, int BS>
+static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pad, cudaStream_t s, PhaseTimer& tm) {
+  const int R = n_pad / BS;
+  const int nT = n_pad / kTile;
+  const size_t ld = (size_t)n_pad;
+  constexpr size_t sm2 = phase2_smem_bytes<T, BS>();
+  constexpr size_t sm3 = std::is_same<T, F32T>::value ? minplus_f32_smem_bytes<BS>() : minplus_u16_smem_bytes<BS>();
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t e1 = cudaFuncSetAttribute(fw_phase2_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    cudaError_t e2;
+    if constexpr (std::is_same<T, F32T>::value)
+      e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    else
+      e2 = cudaFuncSetAttribute(fw_phase3_u16_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    attr_err = e1 != cudaSuccess ? e1 : e2;
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  tm.mark(-1);
+  for (int r = 0; r < R; ++r) {
+    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r);
+    tm.mark(0);
+    if (R > 1) {
+      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R);
+      tm.mark(1);
+      if constexpr (std::is_same<T, F32T>::value)
+        fw_phase3_f32_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r);
+      else
+        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r);
+      tm.mark(2);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, int bs, cudaStream_t s,
+                                 PhaseTimer& tm) {
+  switch (bs) {
+    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm);
+    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm);
+    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- planning
+
+struct Plan {
+  int n = 0, n_pad = 0, bs = 0, dtype = 0;
+  bool in_place = false;
+  size_t ws_stats = 0, ws_d = 0, ws_p = 0, ws_total = 0;  // byte offsets / total
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Workspace layout for a given arithmetic: [stats][D work][P work].
+static void layout(Plan& pl, bool p_in_place) {
+  const size_t np2 = (size_t)pl.n_pad * pl.n_pad;
+  size_t off = 0;
+  pl.ws_stats = off;
+  off = align256(off + sizeof(WeightStats));
+  pl.ws_d = off;
+  if (pl.dtype == APSP_DTYPE_U16X2) off = align256(off + np2 * sizeof(uint16_t));
+  else if (!pl.in_place) off = align256(off + np2 * sizeof(float));
+  pl.ws_p = off;
+  if (!p_in_place) off = align256(off + np2 * sizeof(int32_t));
+  pl.ws_total = off;
+}
+
+int padded_order(int n) { return ((n + kTile - 1) / kTile) * kTile; }
+
+}  // namespace apsp
+
+using namespace apsp;
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" int apsp_default_bs(int n) {
+  if (n <= 2048) return 32;
+  return 64;
+}
+
+extern "C" const char* apsp_status_str(apsp_status s) {
+  switch (s) {
+    case APSP_OK: return "ok";
+    case APSP_EINVAL: return "invalid argument";
+    case APSP_ENOMEM: return "out of memory";
+    case APSP_ECUDA: return "CUDA error";
+    case APSP_ETIMEOUT: return "timed out";
+    case APSP_EBUSY: return "busy / not ready";
+    case APSP_ECANCELLED: return "cancelled";
+    case APSP_ENOTFOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+static apsp_options default_options() {
+  apsp_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.bs = 0;
+  o.dtype = APSP_DTYPE_AUTO;
+  o.validate = 1;
+  return o;
+}
+
+static bool valid_bs(int bs) { return bs == 32 || bs == 64 || bs == 128; }
+
+extern "C" size_t apsp_fw_workspace_size(int n, const apsp_options* opt) {
+  apsp_options o = opt ? *opt : default_options();
+  if (n < 1) return 0;
+  Plan pl;
+  pl.n = n;
+  pl.n_pad = padded_order(n);
+  const bool pad = pl.n_pad != n;
+  // F32 working set
+  pl.dtype = APSP_DTYPE_F32;
+  pl.in_place = !pad;
+  layout(pl, !pad);
+  size_t f32 = pl.ws_total;
+  if (o.dtype == APSP_DTYPE_F32) return f32;
+  pl.dtype = APSP_DTYPE_U16X2;
+  pl.in_place = false;
+  layout(pl, !pad);
+  return std::max(f32, pl.ws_total);
+}
+
+namespace apsp {
+
+// Scan W and decide the arithmetic. Synchronises `s` once.
+static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats* dstats, cudaStream_t s, int* dtype_out) {
+  if (cudaMemsetAsync(dstats, 0, sizeof(WeightStats), s) != cudaSuccess) return APSP_ECUDA;
+  scan_weights_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(W, n, dstats);
+  WeightStats hs;
+  if (cudaMemcpyAsync(&hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return APSP_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return APSP_ECUDA;
+  if (hs.n_negative || hs.n_nan) return APSP_EINVAL;
+  float mx;
+  std::memcpy(&mx, &hs.max_bits, sizeof(mx));
+  const bool eligible = hs.n_fraction == 0 && (double)mx * (double)(n - 1) < 65535.0;
+  if (want == APSP_DTYPE_U16X2 && !eligible) return APSP_EINVAL;
+  *dtype_out = (want == APSP_DTYPE_F32) ? APSP_DTYPE_F32 : (eligible ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32);
+  return APSP_OK;
+}
+
+apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
+                   size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
+  apsp_options o = opt ? *opt : default_options();
+  if (n < 1 || !W || !D || !P) return APSP_EINVAL;
+  if (o.bs == 0) o.bs = apsp_default_bs(n);
+  if (!valid_bs(o.bs)) return APSP_EINVAL;
+  if (o.dtype < APSP_DTYPE_AUTO || o.dtype > APSP_DTYPE_U16X2) return APSP_EINVAL;
+  if (!o.validate && o.dtype != APSP_DTYPE_F32) return APSP_EINVAL;
+  if (n > 65536) return APSP_EINVAL;
+
+  Plan pl;
+  pl.n = n;
+  pl.n_pad = padded_order(n);
+  pl.bs = o.bs;
+  const bool pad = pl.n_pad != n;
+
+  // Workspace: caller's, or stream-ordered allocation of the largest need.
+  void* ws = workspace;
+  bool own_ws = false;
+  const size_t need_max = std::max<size_t>(apsp_fw_workspace_size(n, &o), 256);
+  if (ws == nullptr) {
+    if (cudaMallocAsync(&ws, need_max, s) != cudaSuccess) {
+      cudaGetLastError();
+      return APSP_ENOMEM;
+    }
+    own_ws = true;
+    workspace_bytes = need_max;
+  }
+  if (((uintptr_t)ws & 255) != 0) return APSP_EINVAL;
+  auto fail = [&](apsp_status st) {
+    if (own_ws) cudaFreeAsync(ws, s);
+    return st;
+  };
+
+  int dtype = APSP_DTYPE_F32;
+  if (o.validate) {
+    if (workspace_bytes < sizeof(WeightStats)) return fail(APSP_ENOMEM);
+    apsp_status st = scan_and_choose(W, n, o.dtype, reinterpret_cast<WeightStats*>(ws), s, &dtype);
+    if (st != APSP_OK) return fail(st);
+  }
+  pl.dtype = dtype;
+  const bool p_in_place = !pad && aligned16(P);
+  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad && aligned16(D);
+  layout(pl, p_in_place);
+  if (workspace_bytes < pl.ws_total) return fail(APSP_ENOMEM);
+
+  char* wsb = static_cast<char*>(ws);
+  int32_t* Pw = p_in_place ? P : reinterpret_cast<int32_t*>(wsb + pl.ws_p);
+  const size_t quads = (size_t)pl.n_pad * (pl.n_pad / 4);
+  PhaseTimer tm;
+  tm.s = s;
+  tm.on = (o.flags & APSP_FLAG_TIME_PHASES) != 0;
+  int aux = o.validate ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  if (dtype == APSP_DTYPE_F32) {
+    float* Dw = pl.in_place ? D : reinterpret_cast<float*>(wsb + pl.ws_d);
+    init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
+    ++aux;
+    e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm);
+    if (e == cudaSuccess && !pl.in_place) {
+      copy_out_kernel<float><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
+      ++aux;
+    }
+  } else {
+    uint16_t* Dw = reinterpret_cast<uint16_t*>(wsb + pl.ws_d);
+    init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
+    ++aux;
+    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm);
+    if (e == cudaSuccess) {
+      widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
+      ++aux;
+    }
+  }
+  if (e == cudaSuccess && !p_in_place) {
+    copy_out_kernel<int32_t><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Pw, pl.n_pad, P, n);
+    ++aux;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  float ms[3];
+  tm.finish(ms);
+  if (own_ws) cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return APSP_ECUDA;
+  if (info) {
+    info->bs_used = pl.bs;
+    info->dtype_used = dtype;
+    info->rounds = pl.n_pad / pl.bs;
+    info->n_pad = pl.n_pad;
+    info->launches = aux + tm.launches[0] + tm.launches[1] + tm.launches[2];
+    for (int q = 0; q < 3; ++q) {
+      info->phase_launches[q] = tm.launches[q];
+      info->phase_ms[q] = ms[q];
+    }
+  }
+  return APSP_OK;
+}
+
+}  // namespace apsp
+
+extern "C" apsp_status apsp_fw_ex(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
+                                  size_t workspace_bytes, apsp_run_info* info, void* stream) {
+  return fw_run(W, D, P, n, opt, workspace, workspace_bytes, info, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" apsp_status apsp_fw(const float* W, float* D, int32_t* P, int n, void* stream) {
+  return fw_run(W, D, P, n, nullptr, nullptr, 0, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
+                                    apsp_run_info* info, void* stream) {
+  if (n < 1 || !W || !D || !P) return APSP_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)n * n * sizeof(float);
+  float *dW = nullptr, *dD = nullptr;
+  int32_t* dP = nullptr;
+  if (cudaMallocAsync(&dW, bytes, s) != cudaSuccess || cudaMallocAsync(&dD, bytes, s) != cudaSuccess ||
+      cudaMallocAsync(&dP, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (dW) cudaFreeAsync(dW, s);
+    if (dD) cudaFreeAsync(dD, s);
+    cudaStreamSynchronize(s);
+    return APSP_ENOMEM;
+  }
+  apsp_status st = APSP_OK;
+  if (cudaMemcpyAsync(dW, W, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) st = APSP_ECUDA;
+  if (st == APSP_OK) st = fw_run(dW, dD, dP, n, opt, nullptr, 0, info, s);
+  if (st == APSP_OK) {
+    if (cudaMemcpyAsync(D, dD, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = APSP_ECUDA;
+  }
+  cudaFreeAsync(dW, s);
+  cudaFreeAsync(dD, s);
+  cudaFreeAsync(dP, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == APSP_OK) st = APSP_ECUDA;
+  return st;
+}

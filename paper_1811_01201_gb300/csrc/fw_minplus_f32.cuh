@@ -1,0 +1,235 @@
+// Phase 3 of a block round, fp32: every tile outside row r and column r.
+//
+// Section 4.1 of arXiv 1811.01201 (paper phase 4): each remaining block
+// (I,J) depends only on block (I,r) of its row and block (r,J) of its column,
+// which phase 3 never changes. FW_BLOCK (Section 4.2) relaxes every element
+// through k = kb .. kb+BS-1 in ascending order with a strict '<' and records
+// the global k in P (Section 3).
+//
+// With both panels fixed, the serial strict-'<' sweep over k has a closed
+// form per element: D' = min(D, min_k (A[i][k] + B[k][j])) (fp32 min is exact
+// and order-free), and P changes only if D' < D, to kb + the FIRST k whose
+// candidate equals D'. The kernel therefore runs the hot loop as one FADD and
+// one FMNMX per update and recovers P afterwards:
+//
+//  * integer-valued tile panels whose largest finite sum stays within a bound:
+//    every operand is scaled by M = 2*BS and the A panel carries k+1 in the
+//    low bits (A' = M*a + k + 1, B' = M*b, D' = M*d; k+1 <= BS < M). The
+//    candidate keys M*(a+b) + k + 1 are exact while below 2^24, so min over
+//    keys yields the minimum value and, among equal values, the smallest k --
+//    while the old D (slot 0) wins ties, as the strict '<' requires. P comes
+//    for free.
+//  * otherwise (real-valued weights, large distances): improved elements are
+//    found by comparing with the old D, and each warp re-evaluates the BS
+//    candidates of one improved element at a time, one k per lane, taking
+//    the first lane whose sum equals D' (bit-identical FADD, so equality is
+//    exact).
+//
+// Tiling: 128 x 128 output tile per CTA of 256 threads, 8 x 8 elements per
+// thread in registers (rows ty*4+{0..3}, 64+ty*4+{0..3}; columns likewise
+// with tx). The A panel slice (128 x BS) is stored transposed and the B panel
+// slice (BS x 128) as is, both with a padded row stride of 132 floats, so the
+// per-k fragment loads are 128-bit and conflict-free. Rows/columns of the
+// tile that fall in block r (the panels) are computed but never written.
+#pragma once
+
+#include "fw_common.cuh"
+
+namespace apsp {
+
+constexpr int kSst = kTile + 4;  // shared row stride (floats)
+
+// Key scale M = 2*BS (a power of two, so scaling is exact) and the largest
+// finite panel sum a + b for which every key M*(a+b) + BS stays below 2^24.
+template <int BS>
+struct KeyParams {
+  static constexpr float M = 2.0f * BS;
+  static constexpr float bound = (float)(((1 << 24) - 2 * BS) / (2 * BS) - 16);
+  static_assert(BS == 32 || BS == 64 || BS == 128, "unsupported block size");
+};
+
+template <int BS>
+constexpr size_t minplus_f32_smem_bytes() {
+  return sizeof(float) * 2 * (size_t)BS * kSst;
+}
+
+__device__ __forceinline__ int mp_row(int ty, int a) { return (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
+__device__ __forceinline__ int mp_col(int tx, int c) { return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
+
+__device__ __forceinline__ bool is_int_or_inf(float v) { return !(v < f32_inf()) || v == floorf(v); }
+
+template <int BS>
+__global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
+                                                               size_t ld, int nT, int r) {
+  extern __shared__ __align__(16) float sm[];
+  float* As = sm;              // As[k * kSst + i] = D[r0 + i][kb + k]
+  float* Bs = sm + BS * kSst;  // Bs[k * kSst + j] = D[kb + k][c0 + j]
+  __shared__ int s_maxA, s_maxB, s_frac;
+
+  const int kb = r * BS;
+  const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
+  const int r0 = tr * kTile, c0 = tc * kTile;
+  // Tiles entirely inside row band r or column band r belong to phases 1-2.
+  if (r0 >= kb && r0 + kTile <= kb + BS) return;
+  if (c0 >= kb && c0 + kTile <= kb + BS) return;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) { s_maxA = 0; s_maxB = 0; s_frac = 0; }
+
+  // C tile -> registers (16 x 128-bit loads, coalesced along rows).
+  float d[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const float* row = D + (size_t)(r0 + mp_row(ty, a)) * ld + c0;
+    const float4 v0 = *reinterpret_cast<const float4*>(row + tx * 4);
+    const float4 v1 = *reinterpret_cast<const float4*>(row + 64 + tx * 4);
+    d[a][0] = v0.x; d[a][1] = v0.y; d[a][2] = v0.z; d[a][3] = v0.w;
+    d[a][4] = v1.x; d[a][5] = v1.y; d[a][6] = v1.z; d[a][7] = v1.w;
+  }
+
+  // B panel slice: BS rows x 128 columns, 128-bit loads and stores.
+  float mxb = 0.f, mxa = 0.f;
+  bool frac = false;
+#pragma unroll
+  for (int m = 0; m < BS / 8; ++m) {
+    const int idx = tid + 256 * m, k = idx >> 5, q = idx & 31;
+    const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(kb + k) * ld + c0 + q * 4);
+    *reinterpret_cast<float4*>(Bs + k * kSst + q * 4) = v;
+    mxb = fmaxf(mxb, fmaxf(fmaxf(v.x < f32_inf() ? v.x : 0.f, v.y < f32_inf() ? v.y : 0.f),
+                           fmaxf(v.z < f32_inf() ? v.z : 0.f, v.w < f32_inf() ? v.w : 0.f)));
+    frac |= !(is_int_or_inf(v.x) && is_int_or_inf(v.y) && is_int_or_inf(v.z) && is_int_or_inf(v.w));
+  }
+  // A panel slice: 128 rows x BS columns, stored transposed. Lane -> (row
+  // ri = lane & 7 of an 8-row group, column quad cq = lane >> 3).
+#pragma unroll
+  for (int m = 0; m < BS / 8; ++m) {
+    const int idx = tid + 256 * m;
+    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;  // grp: 0 .. 4*BS/8-1
+    const int rows_per_pass = 8;
+    const int quads = BS / 4;
+    const int i = (grp % (kTile / rows_per_pass)) * rows_per_pass + ri;
+    const int q4 = (grp / (kTile / rows_per_pass)) * 4 + cq;
+    if (q4 < quads) {
+      const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
+      As[(q4 * 4 + 0) * kSst + i] = v.x;
+      As[(q4 * 4 + 1) * kSst + i] = v.y;
+      As[(q4 * 4 + 2) * kSst + i] = v.z;
+      As[(q4 * 4 + 3) * kSst + i] = v.w;
+      mxa = fmaxf(mxa, fmaxf(fmaxf(v.x < f32_inf() ? v.x : 0.f, v.y < f32_inf() ? v.y : 0.f),
+                             fmaxf(v.z < f32_inf() ? v.z : 0.f, v.w < f32_inf() ? v.w : 0.f)));
+      frac |= !(is_int_or_inf(v.x) && is_int_or_inf(v.y) && is_int_or_inf(v.z) && is_int_or_inf(v.w));
+    }
+  }
+  __syncthreads();  // s_* initialised
+  atomicMax(&s_maxA, __float_as_int(mxa));
+  atomicMax(&s_maxB, __float_as_int(mxb));
+  if (frac) s_frac = 1;
+  __syncthreads();
+  constexpr float M = KeyParams<BS>::M;
+  const bool keyed =
+      (s_frac == 0) && (__int_as_float(s_maxA) + __int_as_float(s_maxB) <= KeyParams<BS>::bound);
+
+  if (keyed) {
+    // A' = M a + (k + 1), B' = M b, D' = M d (all exact).
+    for (int t = tid; t < BS * kTile; t += 256) {
+      const int k = t / kTile, i = t - k * kTile;
+      As[k * kSst + i] = fmaf(As[k * kSst + i], M, (float)(k + 1));
+      Bs[k * kSst + i] = Bs[k * kSst + i] * M;
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) d[a][c] *= M;
+    __syncthreads();
+  }
+
+  // Hot loop: 64 independent FADD + FMNMX chains per thread per k.
+  const float* Ap = As + ty * 4;
+  const float* Bp = Bs + tx * 4;
+#pragma unroll 4
+  for (int k = 0; k < BS; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * kSst);
+    const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * kSst + 64);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bp + k * kSst);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bp + k * kSst + 64);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
+  }
+
+  // Epilogue: compare with the old tile (re-read; still in L2), write back
+  // only changed 4-element groups, never rows/columns of block r.
+  uint64_t imp = 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int gi = r0 + mp_row(ty, a);
+    const bool band_r = (gi >= kb) && (gi < kb + BS);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gj = c0 + mp_col(tx, 4 * h);
+      const bool band_c = (gj >= kb) && (gj < kb + BS);
+      if (band_r || band_c) continue;
+      float* dp = D + (size_t)gi * ld + gj;
+      const float4 o4 = *reinterpret_cast<const float4*>(dp);
+      const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+      float nv[4];
+      bool any = false;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float dn = d[a][4 * h + e];
+        if (keyed) {
+          const bool im = dn < old[e] * M;
+          if (im) {
+            const float v = floorf(dn * (1.f / M));
+            const int s = (int)(dn - v * M);
+            nv[e] = v;
+            P[(size_t)gi * ld + gj + e] = kb + s - 1;
+          } else {
+            nv[e] = old[e];
+          }
+          any |= im;
+        } else {
+          const bool im = dn < old[e];
+          nv[e] = im ? dn : old[e];
+          if (im) imp |= 1ull << (a * 8 + 4 * h + e);
+          any |= im;
+        }
+      }
+      if (any) *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+    }
+  }
+  if (keyed) return;
+
+  // Generic path: recover P for each improved element, one warp per element,
+  // one candidate k per lane.
+  if (!__any_sync(0xffffffffu, imp != 0)) return;
+#pragma unroll
+  for (int slot = 0; slot < 64; ++slot) {
+    unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);
+    if (!bal) continue;
+    const int a = slot >> 3, c = slot & 7;
+    const float dmine = d[a][c];
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int stid = warp * 32 + src;
+      const int li = mp_row(stid >> 4, a), lj = mp_col(stid & 15, c);
+      const float dn = __shfl_sync(0xffffffffu, dmine, src);
+      int kstar = BS;
+#pragma unroll
+      for (int m = 0; m < BS / 32; ++m) {
+        const int k = m * 32 + lane;
+        const float cand = __fadd_rn(As[k * kSst + li], Bs[k * kSst + lj]);
+        const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
+        if (eq && kstar == BS) kstar = m * 32 + __ffs(eq) - 1;
+      }
+      if (lane == src) P[(size_t)(r0 + li) * ld + c0 + lj] = kb + kstar;
+    }
+  }
+}
+
+}  // namespace apsp

@@ -1,0 +1,192 @@
+// Phase 3 of a block round on exact 16-bit distances, two per 32-bit lane.
+//
+// Same update as the fp32 kernel (Section 4.1 paper phase 4, Section 4.2
+// FW_BLOCK with strict '<', P = global k per Section 3), on integer distances
+// stored as uint16 with 0xFFFF = INF. A graph qualifies for this path only
+// when every path length is below 0xFFFF (max_w * (n-1) < 65535), so the
+// saturating sum min(a + b, 0xFFFF) equals the exact sum whenever it can
+// matter, and D and P come out bit-identical to the fp32 path.
+//
+// The hot loop is PTX add.u16x2 + min.u16x2: two updates per instruction
+// pair. A wrapping add is exact when no a + b in the tile can exceed 0xFFFF,
+// which the kernel checks per tile from the panel maxima; tiles that could
+// overflow (typically panels still holding INF) use the saturating form
+// sat(a + b) = min(a, ~b) + b (one more min per pair).
+//
+// P is recovered as in the fp32 generic path: an element improved iff its new
+// value is below the old one; a warp then re-evaluates its BS candidates, one
+// k per lane, and takes the first k whose saturated sum equals the new value.
+//
+// Tiling: 128 x 128 output tile per CTA of 256 threads; each thread owns 8
+// rows (ty*4+{0..3}, 64+ty*4+{0..3}) x 8 consecutive columns (tx*8 ..), i.e.
+// 8 x 4 packed words. The A panel slice is stored transposed with every value
+// duplicated into both halves of a word; the B panel slice as is.
+#pragma once
+
+#include "fw_common.cuh"
+#include "fw_minplus_f32.cuh"
+
+namespace apsp {
+
+constexpr int kSstA16 = kTile + 4;      // words per transposed-A row
+constexpr int kSstB16 = kTile / 2 + 4;  // words per B row (two uint16 per word)
+
+template <int BS>
+constexpr size_t minplus_u16_smem_bytes() {
+  return sizeof(uint32_t) * (size_t)BS * (kSstA16 + kSstB16);
+}
+
+__device__ __forceinline__ uint32_t vadd16(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("add.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t vmin16(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t umax4(uint4 v) {
+  // largest of the eight uint16 lanes of v
+  uint32_t m = max(max(max(v.x & 0xFFFF, v.x >> 16), max(v.y & 0xFFFF, v.y >> 16)),
+                   max(max(v.z & 0xFFFF, v.z >> 16), max(v.w & 0xFFFF, v.w >> 16)));
+  return m;
+}
+
+template <int BS, bool SAT>
+__device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint32_t* __restrict__ Ap,
+                                                 const uint32_t* __restrict__ Bp) {
+#pragma unroll 4
+  for (int k = 0; k < BS; ++k) {
+    const uint4 a0 = *reinterpret_cast<const uint4*>(Ap + k * kSstA16);
+    const uint4 a1 = *reinterpret_cast<const uint4*>(Ap + k * kSstA16 + 64);
+    const uint4 b4 = *reinterpret_cast<const uint4*>(Bp + k * kSstB16);
+    const uint32_t av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
+    uint32_t nb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nb[q] = ~bv[q];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t s = SAT ? vadd16(vmin16(av[a], nb[q]), bv[q]) : vadd16(av[a], bv[q]);
+        w[a][q] = vmin16(w[a][q], s);
+      }
+  }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restrict__ D, int32_t* __restrict__ P,
+                                                               size_t ld, int nT, int r) {
+  extern __shared__ __align__(16) uint32_t smu[];
+  uint32_t* As = smu;                 // As[k * kSstA16 + i] = dup(D[r0 + i][kb + k])
+  uint32_t* Bs = smu + BS * kSstA16;  // Bs[k * kSstB16 + q] = D[kb + k][c0 + 2q .. 2q+1]
+  __shared__ unsigned s_ma, s_mb;
+
+  const int kb = r * BS;
+  const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
+  const int r0 = tr * kTile, c0 = tc * kTile;
+  if (r0 >= kb && r0 + kTile <= kb + BS) return;
+  if (c0 >= kb && c0 + kTile <= kb + BS) return;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) { s_ma = 0; s_mb = 0; }
+
+  uint32_t w[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(r0 + mp_row(ty, a)) * ld + c0 + tx * 8);
+    w[a][0] = v.x; w[a][1] = v.y; w[a][2] = v.z; w[a][3] = v.w;
+  }
+
+  uint32_t mxa = 0, mxb = 0;
+  // B slice: BS rows x 128 uint16 = 16 uint4 per row.
+#pragma unroll
+  for (int m = 0; m < BS / 16; ++m) {
+    const int idx = tid + 256 * m, k = idx >> 4, q = idx & 15;
+    const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
+    *reinterpret_cast<uint4*>(Bs + k * kSstB16 + q * 4) = v;
+    mxb = max(mxb, umax4(v));
+  }
+  // A slice: 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
+#pragma unroll
+  for (int m = 0; m < BS / 16; ++m) {
+    const int idx = tid + 256 * m;
+    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
+    const int i = (grp & 15) * 8 + ri;
+    const int q8 = (grp >> 4) * 4 + cq;
+    const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(r0 + i) * ld + kb + q8 * 8);
+    const uint32_t h[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t lo = h[e] & 0xFFFF, hi = h[e] >> 16;
+      As[(q8 * 8 + 2 * e) * kSstA16 + i] = lo | (lo << 16);
+      As[(q8 * 8 + 2 * e + 1) * kSstA16 + i] = hi | (hi << 16);
+    }
+    mxa = max(mxa, umax4(v));
+  }
+  __syncthreads();  // s_ma / s_mb initialised
+  atomicMax(&s_ma, mxa);
+  atomicMax(&s_mb, mxb);
+  __syncthreads();
+  const bool sat = (s_ma + s_mb) > 0xFFFFu;
+
+  if (sat)
+    minplus_u16_loop<BS, true>(w, As + ty * 4, Bs + tx * 4);
+  else
+    minplus_u16_loop<BS, false>(w, As + ty * 4, Bs + tx * 4);
+
+  // Epilogue: write back changed 8-element groups outside block r's rows and
+  // columns; flag improved elements (slot = a*8 + column).
+  uint64_t imp = 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int gi = r0 + mp_row(ty, a);
+    const int gj = c0 + tx * 8;
+    if ((gi >= kb && gi < kb + BS) || (gj >= kb && gj < kb + BS)) continue;
+    uint16_t* dp = D + (size_t)gi * ld + gj;
+    const uint4 o4 = *reinterpret_cast<const uint4*>(dp);
+    const uint32_t old[4] = {o4.x, o4.y, o4.z, o4.w};
+    uint32_t nv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t mn = vmin16(w[a][q], old[q]);  // never above old
+      nv[q] = mn;
+      if ((mn & 0xFFFF) < (old[q] & 0xFFFF)) imp |= 1ull << (a * 8 + 2 * q);
+      if ((mn >> 16) < (old[q] >> 16)) imp |= 1ull << (a * 8 + 2 * q + 1);
+    }
+    if (imp >> (a * 8) & 0xFF) *reinterpret_cast<uint4*>(dp) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
+  }
+
+  if (!__any_sync(0xffffffffu, imp != 0)) return;
+#pragma unroll
+  for (int slot = 0; slot < 64; ++slot) {
+    unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);
+    if (!bal) continue;
+    const int a = slot >> 3, c = slot & 7;
+    const uint32_t dmine = (c & 1) ? (w[a][c >> 1] >> 16) : (w[a][c >> 1] & 0xFFFF);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int stid = warp * 32 + src;
+      const int li = mp_row(stid >> 4, a), lj = (stid & 15) * 8 + c;
+      const uint32_t dn = __shfl_sync(0xffffffffu, dmine, src);
+      int kstar = BS;
+#pragma unroll
+      for (int m = 0; m < BS / 32; ++m) {
+        const int k = m * 32 + lane;
+        const uint32_t av = As[k * kSstA16 + li] & 0xFFFF;
+        const uint32_t bw = Bs[k * kSstB16 + (lj >> 1)];
+        const uint32_t bvv = (lj & 1) ? (bw >> 16) : (bw & 0xFFFF);
+        const uint32_t cand = min(av + bvv, kInf16);
+        const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
+        if (eq && kstar == BS) kstar = m * 32 + __ffs(eq) - 1;
+      }
+      if (lane == src) P[(size_t)(r0 + li) * ld + c0 + lj] = kb + kstar;
+    }
+  }
+}
+
+}  // namespace apsp

@@ -1,0 +1,64 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+function that include/apsp.h declares. No compute calls (no GPU here)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1811_01201_gb300 as apsp
+from paper_1811_01201_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(apsp_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_loads():
+    path = _build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    assert lib is not None
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(_build.build())
+    declared = _declared_functions()
+    assert {"apsp_fw", "apsp_fw_ex", "apsp_fw_batched", "apsp_serve_create", "apsp_path"} <= declared
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, f"declared in include/*.h but not exported: {missing}"
+
+
+def test_host_only_helpers():
+    # these touch no GPU state
+    assert apsp.apsp_default_bs(512) in (32, 64, 128)
+    assert apsp.status_str(apsp.APSP_EINVAL) == "invalid argument"
+    assert apsp.apsp_fw_workspace_size(128, dtype=apsp.DTYPE_F32) >= 256
+    assert apsp.apsp_fw_workspace_size(100, dtype=apsp.DTYPE_F32) >= 128 * 128 * 8
+    assert apsp.apsp_fw_workspace_size(0) == 0
+
+
+def test_path_helper_matches_oracle_walk():
+    import oracle
+    from paper_1811_01201_gb300 import inputs
+    n = 70
+    W = inputs.dense_digraph(n, 3, 1, 50, density=0.3).numpy()
+    D, P = oracle.fw_blocked(W, 16)
+    for i in range(0, n, 7):
+        for j in range(0, n, 5):
+            assert apsp.apsp_path(P, i, j) == oracle.path(P, i, j)
+    bad = P.copy()
+    bad[0, 1] = 0  # intermediate equal to an endpoint
+    assert apsp.apsp_path(bad, 0, 1) is None

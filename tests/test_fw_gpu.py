@@ -1,0 +1,293 @@
+"""GPU parity of the single-graph path (apsp_fw / apsp_fw_ex / apsp_fw_host)
+against the serial oracle.
+
+D and P must match oracle.fw_blocked with the same block size bit for bit:
+the kernels perform the same fp32 additions (or exact 16-bit sums) and the
+same strict-'<' first-k choice as the serial loop, for integer and real
+weights alike. At the full benchmark sizes the oracle cannot run the whole
+matrix, so sampled rows are checked against the oracle's Dijkstra (exact for
+integer weights, 1e-5 relative for real weights, the tolerance the workload
+specification states) and sampled pairs against the oracle's P-walk check.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1811_01201_gb300 as apsp
+from paper_1811_01201_gb300 import inputs
+from tests.helpers import all_pairs, load_golden, random_pairs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+INF = float("inf")
+
+
+def _run(W: torch.Tensor, bs=0, dtype=apsp.DTYPE_AUTO, validate=True):
+    n = W.shape[0]
+    Wd = W.to(DEV)
+    D = torch.empty_like(Wd)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    info = apsp.apsp_fw_ex(Wd, D, P, bs=bs, dtype=dtype, validate=validate)
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), P.cpu().numpy(), info
+
+
+def _expect_exact(W, D, P, bs):
+    Dr, Pr = oracle.fw_blocked(W.numpy() if isinstance(W, torch.Tensor) else W, bs)
+    np.testing.assert_array_equal(D, Dr)
+    np.testing.assert_array_equal(P, Pr)
+
+
+# ---------------------------------------------------------------- exact parity, small and ragged n
+
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 32, 33, 127, 128, 129, 200, 256, 300, 384])
+@pytest.mark.parametrize("bs", [32, 64, 128])
+def test_f32_int_weights_bit_exact(n, bs):
+    W = inputs.dense_digraph(n, seed=1000 + n, lo=1, hi=100, density=0.6)
+    D, P, info = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    assert info.bs_used == bs and info.dtype_used == apsp.DTYPE_F32
+    _expect_exact(W, D, P, bs)
+
+
+@pytest.mark.parametrize("n,bs", [(160, 32), (257, 64), (512, 64), (390, 128)])
+def test_f32_real_weights_bit_exact(n, bs):
+    # real weights take the rescan path for P; the fp32 sums are the same ops
+    W = inputs.dense_digraph(n, seed=2000 + n, kind="real", density=0.8)
+    D, P, info = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    _expect_exact(W, D, P, bs)
+
+
+def test_f32_large_distances_take_generic_path():
+    # weights up to 1e6: panel sums exceed the exact-key bound, forcing the rescan path
+    W = inputs.dense_digraph(300, seed=7, lo=1, hi=1_000_000, density=0.3)
+    D, P, _ = _run(W, bs=64, dtype=apsp.DTYPE_F32)
+    _expect_exact(W, D, P, 64)
+
+
+@pytest.mark.parametrize("bs", [32, 64, 128])
+def test_f32_keys_near_exactness_bound(bs):
+    # integer distances close to the largest panel sum the exact-key path accepts for this BS
+    hi = {32: 120000, 64: 60000, 128: 30000}[bs]
+    W = inputs.dense_digraph(300, seed=40 + bs, lo=hi // 2, hi=hi, density=0.4)
+    D, P, _ = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    _expect_exact(W, D, P, bs)
+
+
+def test_config_n512_dense_int():
+    # the small benchmark workload: n=512, integer weights in [1,100], dense
+    W = inputs.dense_digraph(512, seed=1, lo=1, hi=100)
+    for bs in (32, 64):
+        D, P, _ = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+        _expect_exact(W, D, P, bs)
+
+
+@pytest.mark.parametrize("n,hi,bs", [(130, 2, 32), (300, 100, 64), (520, 20, 32), (256, 255, 128)])
+def test_u16_path_bit_exact(n, hi, bs):
+    W = inputs.dense_digraph(n, seed=3000 + n, lo=1, hi=hi, density=0.5)
+    assert hi * (n - 1) < 65535
+    D, P, info = _run(W, bs=bs, dtype=apsp.DTYPE_AUTO)
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    _expect_exact(W, D, P, bs)
+    D2, P2, info2 = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    assert info2.dtype_used == apsp.DTYPE_F32
+    np.testing.assert_array_equal(D, D2)
+    np.testing.assert_array_equal(P, P2)
+
+
+def test_u16_bound_edge():
+    # max_w*(n-1) = 65534 is eligible; one more unit of weight is not
+    n = 257
+    W = inputs.dense_digraph(n, seed=5, lo=1, hi=255, density=1.0)
+    W[0, 1] = 255.0
+    D, P, info = _run(W, bs=32)
+    assert info.dtype_used == apsp.DTYPE_U16X2  # 255 * 256 = 65280 < 65535
+    _expect_exact(W, D, P, 32)
+    W[0, 1] = 300.0  # 300 * 256 = 76800: not eligible
+    D, P, info = _run(W, bs=32)
+    assert info.dtype_used == apsp.DTYPE_F32
+    _expect_exact(W, D, P, 32)
+    with pytest.raises(apsp.ApspError) as e:
+        _run(W, bs=32, dtype=apsp.DTYPE_U16X2)
+    assert e.value.status == apsp.APSP_EINVAL
+
+
+def test_u16_long_chain_saturation():
+    # a directed chain with weight 255 reaches 255*(n-1) = 65280: near the top of the 16-bit range
+    n = 257
+    W = torch.full((n, n), INF)
+    W.fill_diagonal_(0)
+    for t in range(n - 1):
+        W[t, t + 1] = 255
+    W[n - 1, 0] = 1
+    D, P, info = _run(W, bs=32)
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    _expect_exact(W, D, P, 32)
+
+
+# ---------------------------------------------------------------- special graphs and fixtures
+
+@pytest.mark.parametrize("name", ["tie_break_4.txt", "blocked_vs_naive_4.txt"])
+def test_golden_fixtures_on_gpu(name):
+    g = load_golden(name)
+    # the fixtures use BS=2; with BS >= n the run is one round = naive FW
+    D, P, _ = _run(torch.from_numpy(g["W"]), bs=32, dtype=apsp.DTYPE_F32)
+    np.testing.assert_array_equal(D, g["D_naive"])
+    np.testing.assert_array_equal(P, g["P_naive"])
+
+
+def test_all_inf_graph_and_single_vertex():
+    W = torch.full((150, 150), INF)
+    D, P, _ = _run(W, bs=32, dtype=apsp.DTYPE_F32)
+    expect = np.full((150, 150), np.inf, np.float32)
+    np.fill_diagonal(expect, 0)
+    np.testing.assert_array_equal(D, expect)
+    assert (P == -1).all()
+    D, P, _ = _run(torch.zeros((1, 1)), bs=32)
+    assert D[0, 0] == 0 and P[0, 0] == -1
+
+
+def test_complete_unit_graph_no_improvement():
+    n = 200
+    W = torch.ones((n, n))
+    D, P, _ = _run(W, bs=64, dtype=apsp.DTYPE_F32)
+    expect = np.ones((n, n), np.float32)
+    np.fill_diagonal(expect, 0)
+    np.testing.assert_array_equal(D, expect)
+    assert (P == -1).all()
+
+
+def test_nonzero_input_diagonal_is_ignored():
+    W = inputs.dense_digraph(140, seed=9, lo=1, hi=50)
+    W.fill_diagonal_(7.0)
+    D, P, _ = _run(W, bs=32, dtype=apsp.DTYPE_F32)
+    assert (np.diag(D) == 0).all()
+    W0 = W.clone()
+    W0.fill_diagonal_(0)
+    _expect_exact(W0, D, P, 32)
+
+
+# ---------------------------------------------------------------- API behaviour
+
+def test_in_place_and_workspace():
+    n = 256
+    W = inputs.dense_digraph(n, seed=11, lo=1, hi=1000, density=0.5)
+    Dr, Pr = oracle.fw_blocked(W.numpy(), 64)
+    A = W.to(DEV).clone()
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw_ex(A, A, P, bs=64, dtype=apsp.DTYPE_F32)  # W aliases D
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(A.cpu().numpy(), Dr)
+    np.testing.assert_array_equal(P.cpu().numpy(), Pr)
+    n2 = 200
+    W2 = inputs.dense_digraph(n2, seed=12, lo=1, hi=100)
+    ws = torch.empty(apsp.apsp_fw_workspace_size(n2, bs=64), dtype=torch.uint8, device=DEV)
+    D2 = torch.empty((n2, n2), device=DEV)
+    P2 = torch.empty((n2, n2), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw_ex(W2.to(DEV), D2, P2, bs=64, workspace=ws)
+    torch.cuda.synchronize()
+    _expect_exact(W2, D2.cpu().numpy(), P2.cpu().numpy(), 64)
+
+
+def test_default_entry_point_and_stream():
+    n = 333
+    W = inputs.dense_digraph(n, seed=13, lo=1, hi=1000, density=0.7)
+    s = torch.cuda.Stream()
+    Wd = W.to(DEV)
+    D = torch.empty_like(Wd)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        apsp.apsp_fw(Wd, D, P, stream=s)
+    s.synchronize()
+    _expect_exact(W, D.cpu().numpy(), P.cpu().numpy(), apsp.apsp_default_bs(n))
+
+
+def test_host_entry_point():
+    n = 300
+    W = inputs.dense_digraph(n, seed=14, lo=1, hi=1000, density=0.5).pin_memory()
+    D = torch.empty((n, n)).pin_memory()
+    P = torch.empty((n, n), dtype=torch.int32).pin_memory()
+    info = apsp.apsp_fw_host(W, D, P, bs=32)
+    _expect_exact(W, D.numpy(), P.numpy(), info.bs_used)
+
+
+def test_invalid_inputs_rejected():
+    n = 64
+    W = inputs.dense_digraph(n, seed=15, lo=1, hi=10)
+    for bad in (-1.0, float("nan")):
+        Wb = W.clone()
+        Wb[3, 5] = bad
+        with pytest.raises(apsp.ApspError) as e:
+            _run(Wb)
+        assert e.value.status == apsp.APSP_EINVAL
+    with pytest.raises(apsp.ApspError) as e:
+        _run(W, bs=48)
+    assert e.value.status == apsp.APSP_EINVAL
+    with pytest.raises(apsp.ApspError) as e:
+        _run(W, dtype=apsp.DTYPE_U16X2, validate=False)
+    assert e.value.status == apsp.APSP_EINVAL
+    # the context stays usable after rejected calls
+    D, P, _ = _run(W, bs=32)
+    _expect_exact(W, D, P, 32)
+
+
+def test_deterministic_repeats():
+    W = inputs.dense_digraph(384, seed=16, kind="real", density=0.9)
+    D1, P1, _ = _run(W, bs=64, dtype=apsp.DTYPE_F32)
+    D2, P2, _ = _run(W, bs=64, dtype=apsp.DTYPE_F32)
+    assert np.array_equal(D1, D2) and np.array_equal(P1, P2)
+
+
+# ---------------------------------------------------------------- full benchmark sizes (sampled)
+
+def _sampled_check(n, seed, lo, hi, density, kind, bs, n_src=6, n_pairs=20000, dtype=apsp.DTYPE_AUTO,
+                   expect_dtype=None):
+    Wd = inputs.dense_digraph(n, seed, lo, hi, density=density, kind=kind, device=DEV)
+    D = torch.empty_like(Wd)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    info = apsp.apsp_fw_ex(Wd, D, P, bs=bs, dtype=dtype)
+    torch.cuda.synchronize()
+    if expect_dtype is not None:
+        assert info.dtype_used == expect_dtype
+    W = Wd.cpu().numpy()
+    del Wd
+    Dh = D.cpu().numpy()
+    Ph = P.cpu().numpy()
+    del D, P
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(seed)
+    exact = kind == "int"
+    assert (np.diag(Dh) == 0).all()
+    for s in rng.choice(n, size=n_src, replace=False):
+        ref = oracle.dijkstra(W, int(s))
+        row = Dh[s].astype(np.float64)
+        if exact:
+            np.testing.assert_array_equal(row, ref)
+        else:
+            fin = np.isfinite(ref)
+            assert (np.isfinite(row) == fin).all()
+            np.testing.assert_allclose(row[fin], ref[fin], rtol=1e-5)
+        assert oracle.check_bellman_row(W, Dh[s], rtol=0.0 if exact else 1e-5) == 0
+    pairs = random_pairs(n, n_pairs, seed + 1)
+    assert oracle.check_paths(W, Dh, Ph, pairs, rtol=0.0 if exact else 1e-5) == 0
+
+
+def test_full_n8192_int_density_half():
+    _sampled_check(8192, 2, 1, 1000, 0.5, "int", bs=64, expect_dtype=apsp.DTYPE_F32)
+
+
+@pytest.mark.slow
+def test_full_n32768_int():
+    _sampled_check(32768, 3, 1, 1000, 1.0, "int", bs=64, n_src=4, expect_dtype=apsp.DTYPE_F32)
+
+
+@pytest.mark.slow
+def test_full_n32768_real():
+    _sampled_check(32768, 4, 0, 1, 1.0, "real", bs=64, n_src=4, dtype=apsp.DTYPE_F32)
+
+
+@pytest.mark.slow
+def test_full_n32768_u16():
+    _sampled_check(32768, 5, 1, 2, 1.0, "int", bs=64, n_src=4, expect_dtype=apsp.DTYPE_U16X2)
