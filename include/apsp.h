@@ -142,24 +142,42 @@ apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp
                          apsp_run_info* info, void* stream);
 
 /*
- * Many independent graphs in one persistent launch (one CTA works on one
- * graph at a time; graphs are taken largest first from a device work queue).
+ * Many independent graphs in one persistent launch. One CTA runs the whole
+ * blocked Floyd-Warshall (Section 4.1) of one graph at a time and then takes
+ * the next graph from a device work queue (largest first), so thousands of
+ * uneven graphs share the GPU without a launch per graph or per round.
  *   W, D, P: HOST arrays of `count` DEVICE pointers; graph g has order n[g]
  *            (host array), 1 <= n[g] <= APSP_BATCH_MAX_N, row-major with
  *            leading dimension n[g]. W[g] may alias D[g].
- *   opt:     bs must be 0 (per-graph default) or 32; dtype F32 or AUTO (the
- *            batched kernel computes in fp32); validate as above.
+ *   opt:     NULL or bs 0/32 (the batched block size is 32), dtype AUTO/F32
+ *            (computes in fp32), validate 0/1 (1: scan every W for negative
+ *            or NaN weights first).
  *   bs_used: optional HOST array of `count` ints receiving each graph's BS.
- * The call copies a descriptor table to the device through the stream and
- * synchronises `stream` before returning (the table's staging memory is then
- * released). Results equal apsp_fw_ex with bs = bs_used[g], bit for bit.
+ * Synchronises `stream` before returning. Results equal apsp_fw_ex with
+ * bs = bs_used[g] (and dtype F32), bit for bit.
  */
-#define APSP_BATCH_MAX_N 4096
+#define APSP_BATCH_MAX_N 512
 apsp_status apsp_fw_batched(const float* const* W, float* const* D, int32_t* const* P, const int* n, int count,
                             const apsp_options* opt, int* bs_used, void* stream);
 
-/* Block size the batched kernel uses for a graph of order n. */
+/* Block size the batched kernel uses for a graph of order n (32). */
 int apsp_batched_bs(int n);
+
+/*
+ * Reusable batch for repeated or graph-captured launches.
+ * apsp_batch_create validates the arguments as apsp_fw_batched does, uploads
+ * the descriptor table to device memory it owns, and synchronises `stream`.
+ * apsp_batch_launch enqueues the whole batch on `stream` as one queue reset
+ * (a memset) plus ONE persistent kernel launch; it allocates nothing and does
+ * not synchronise, so it may be captured into a CUDA graph and replayed. The
+ * W/D/P buffers named at creation must stay valid while launches run.
+ * apsp_batch_destroy frees the table (after the caller's last launch ended).
+ */
+typedef struct apsp_batch apsp_batch;
+apsp_status apsp_batch_create(const float* const* W, float* const* D, int32_t* const* P, const int* n, int count,
+                              const apsp_options* opt, apsp_batch** out, void* stream);
+apsp_status apsp_batch_launch(apsp_batch* b, void* stream);
+apsp_status apsp_batch_destroy(apsp_batch* b);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -103,6 +103,14 @@ def load(build_if_missing: bool = True):
         L.apsp_fw_batched.restype = c_int
         L.apsp_batched_bs.argtypes = [c_int]
         L.apsp_batched_bs.restype = c_int
+        L.apsp_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(c_int), c_int, ctypes.POINTER(apsp_options),
+                                        ctypes.POINTER(vp), vp]
+        L.apsp_batch_create.restype = c_int
+        L.apsp_batch_launch.argtypes = [vp, vp]
+        L.apsp_batch_launch.restype = c_int
+        L.apsp_batch_destroy.argtypes = [vp]
+        L.apsp_batch_destroy.restype = c_int
     if hasattr(L, "apsp_serve_create"):
         L.apsp_serve_create.argtypes = [ctypes.POINTER(vp), c_size, c_int]
         L.apsp_serve_create.restype = c_int
@@ -227,6 +235,46 @@ def apsp_fw_batched(Ws: Sequence[torch.Tensor], Ds: Sequence[torch.Tensor], Ps: 
     _check(L.apsp_fw_batched(w_arr, d_arr, p_arr, n_arr, count, ctypes.byref(o), bs_arr, _stream_ptr(stream)),
            "apsp_fw_batched")
     return list(bs_arr)
+
+
+class Batch:
+    """apsp_batch_*: a reusable batch; launch() is one queue reset + one kernel (graph-capturable)."""
+
+    def __init__(self, Ws: Sequence[torch.Tensor], Ds: Sequence[torch.Tensor], Ps: Sequence[torch.Tensor],
+                 validate: bool = True, stream=None):
+        L = load()
+        count = len(Ws)
+        if not (len(Ds) == len(Ps) == count):
+            raise ValueError("Ws, Ds, Ps must have the same length")
+        vp = ctypes.c_void_p
+        w_arr, d_arr, p_arr = (vp * count)(), (vp * count)(), (vp * count)()
+        n_arr = (ctypes.c_int * count)()
+        for g in range(count):
+            n = int(Ws[g].shape[0])
+            n_arr[g] = n
+            w_arr[g] = _dev_ptr(Ws[g], torch.float32, n, f"W[{g}]")
+            d_arr[g] = _dev_ptr(Ds[g], torch.float32, n, f"D[{g}]")
+            p_arr[g] = _dev_ptr(Ps[g], torch.int32, n, f"P[{g}]")
+        o = _opts(0, DTYPE_F32, validate)
+        h = vp()
+        _check(L.apsp_batch_create(w_arr, d_arr, p_arr, n_arr, count, ctypes.byref(o), ctypes.byref(h),
+                                   _stream_ptr(stream)), "apsp_batch_create")
+        self._h = h
+        self._keep = (list(Ws), list(Ds), list(Ps))  # buffers must outlive launches
+
+    def launch(self, stream=None) -> None:
+        _check(load().apsp_batch_launch(self._h, _stream_ptr(stream)), "apsp_batch_launch")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().apsp_batch_destroy(self._h), "apsp_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apsp_path(P: np.ndarray | torch.Tensor, i: int, j: int) -> list[int] | None:

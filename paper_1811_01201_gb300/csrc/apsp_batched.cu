@@ -1,0 +1,205 @@
+// Batched APSP: host side of the persistent many-graph launch (C ABI in
+// include/apsp.h). The descriptor table and the largest-first order live in
+// device memory owned by an apsp_batch; a launch is a queue reset plus one
+// kernel, so it can be captured into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/apsp.h"
+#include "apsp_internal.h"
+#include "fw_batched.cuh"
+
+namespace apsp {
+
+// One CTA per graph: count negative / NaN off-diagonal weights.
+__global__ void scan_batch_kernel(const BatchGraph* __restrict__ graphs, int count, unsigned* bad) {
+  __shared__ unsigned s_bad;
+  for (int g = blockIdx.x; g < count; g += gridDim.x) {
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const BatchGraph G = graphs[g];
+    unsigned b = 0;
+    for (size_t t = threadIdx.x; t < (size_t)G.n * G.n; t += blockDim.x) {
+      const size_t i = t / G.n, j = t - i * G.n;
+      const float v = G.W[t];
+      if (i != j && (v != v || v < 0.f)) b = 1;
+    }
+    if (b) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_bad) atomicAdd(bad, 1u);
+    __syncthreads();
+  }
+}
+
+}  // namespace apsp
+
+using namespace apsp;
+
+struct apsp_batch {
+  BatchGraph* d_graphs = nullptr;
+  int* d_order = nullptr;
+  BatchQueue* d_queue = nullptr;
+  int count = 0;
+  int n_max = 0;
+  int ldp = 0;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+extern "C" int apsp_batched_bs(int /*n*/) { return kBBS; }
+
+static apsp_status batch_free(apsp_batch* b) {
+  if (!b) return APSP_OK;
+  cudaFree(b->d_graphs);
+  cudaFree(b->d_order);
+  cudaFree(b->d_queue);
+  delete b;
+  return APSP_OK;
+}
+
+extern "C" apsp_status apsp_batch_create(const float* const* W, float* const* D, int32_t* const* P, const int* n,
+                                         int count, const apsp_options* opt, apsp_batch** out, void* stream) {
+  if (!out) return APSP_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !W || !D || !P || !n) return APSP_EINVAL;
+  int validate = 1;
+  if (opt) {
+    if (opt->bs != 0 && opt->bs != kBBS) return APSP_EINVAL;
+    if (opt->dtype != APSP_DTYPE_AUTO && opt->dtype != APSP_DTYPE_F32) return APSP_EINVAL;
+    validate = opt->validate;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<BatchGraph> hg(count);
+  int n_max = 1;
+  for (int g = 0; g < count; ++g) {
+    if (n[g] < 1 || n[g] > kBMaxN || !W[g] || !D[g] || !P[g]) return APSP_EINVAL;
+    hg[g] = BatchGraph{W[g], D[g], P[g], n[g], 0};
+    n_max = std::max(n_max, n[g]);
+  }
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+
+  apsp_batch* b = new apsp_batch();
+  b->count = count;
+  b->n_max = n_max;
+  b->ldp = batched_ldp(n_max);
+  b->smem = batched_smem_bytes(n_max);
+  if (cudaMalloc(&b->d_graphs, sizeof(BatchGraph) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_queue, sizeof(BatchQueue) + sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    return APSP_ENOMEM;
+  }
+  apsp_status st = APSP_OK;
+  if (cudaMemcpyAsync(b->d_graphs, hg.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = APSP_ECUDA;
+  if (st == APSP_OK && validate) {
+    unsigned* d_bad = reinterpret_cast<unsigned*>(b->d_queue + 1);
+    cudaMemsetAsync(d_bad, 0, sizeof(unsigned), s);
+    scan_batch_kernel<<<std::min(count, sm_count() * 8), 256, 0, s>>>(b->d_graphs, count, d_bad);
+    unsigned h_bad = 0;
+    if (cudaMemcpyAsync(&h_bad, d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) st = APSP_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = APSP_ECUDA;
+    if (st == APSP_OK && h_bad) st = APSP_EINVAL;
+  } else if (st == APSP_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    st = APSP_ECUDA;
+  }
+  if (st == APSP_OK) {
+    if (cudaFuncSetAttribute(fw_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batched_smem_bytes(kBMaxN)) != cudaSuccess)
+      st = APSP_ECUDA;
+    int per_sm = 0;
+    if (st == APSP_OK &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, b->smem) != cudaSuccess)
+      st = APSP_ECUDA;
+    b->grid = std::max(1, std::min(count, std::max(1, per_sm) * sm_count()));
+  }
+  if (st != APSP_OK) {
+    cudaGetLastError();
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return APSP_OK;
+}
+
+extern "C" apsp_status apsp_batch_launch(apsp_batch* b, void* stream) {
+  if (!b) return APSP_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), s) != cudaSuccess) return APSP_ECUDA;
+  fw_batched_kernel<<<b->grid, kBThreads, b->smem, s>>>(b->d_graphs, b->d_order, b->count, b->d_queue, b->ldp);
+  return cudaGetLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+extern "C" apsp_status apsp_batch_destroy(apsp_batch* b) { return batch_free(b); }
+
+namespace apsp {
+
+// Asynchronous one-shot batch for callers that already validated the graphs
+// (the server): descriptor table, order and queue go into one stream-ordered
+// allocation that is released on the same stream after the kernel.
+// host_graphs must be page-locked and stay valid until the stream passes it.
+apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cudaStream_t s) {
+  if (count < 1) return APSP_OK;
+  int n_max = 1;
+  for (int g = 0; g < count; ++g) {
+    if (host_graphs[g].n < 1 || host_graphs[g].n > kBMaxN) return APSP_EINVAL;
+    n_max = std::max(n_max, host_graphs[g].n);
+  }
+  static_assert(sizeof(BatchGraphDesc) == sizeof(BatchGraph), "descriptor layouts differ");
+  const size_t tbl = sizeof(BatchGraph) * count, ord = sizeof(int) * count;
+  const size_t bytes = ((tbl + 255) & ~(size_t)255) + ((ord + 255) & ~(size_t)255) + 256;
+  char* buf = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&buf), bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return APSP_ENOMEM;
+  }
+  BatchGraph* d_graphs = reinterpret_cast<BatchGraph*>(buf);
+  int* d_order = reinterpret_cast<int*>(buf + ((tbl + 255) & ~(size_t)255));
+  BatchQueue* d_q = reinterpret_cast<BatchQueue*>(buf + ((tbl + 255) & ~(size_t)255) + ((ord + 255) & ~(size_t)255));
+  // host_graphs is already in the caller's order; the order array is the identity
+  // (the caller sorts largest first). It is written from a page-locked table
+  // that follows the descriptors in the caller's staging block.
+  const int* host_order = reinterpret_cast<const int*>(host_graphs + count);
+  cudaError_t e = cudaMemcpyAsync(d_graphs, host_graphs, tbl, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, host_order, ord, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_q, 0, sizeof(BatchQueue), s);
+  const size_t smem = batched_smem_bytes(n_max);
+  static bool attr_done = false;
+  if (e == cudaSuccess && !attr_done) {
+    e = cudaFuncSetAttribute(fw_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batched_smem_bytes(kBMaxN));
+    attr_done = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, smem);
+    const int grid = std::max(1, std::min(count, std::max(1, per_sm) * sm_count()));
+    fw_batched_kernel<<<grid, kBThreads, smem, s>>>(d_graphs, d_order, count, d_q, batched_ldp(n_max));
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(buf, s);
+  return e == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+}  // namespace apsp
+
+extern "C" apsp_status apsp_fw_batched(const float* const* W, float* const* D, int32_t* const* P, const int* n,
+                                       int count, const apsp_options* opt, int* bs_used, void* stream) {
+  apsp_batch* b = nullptr;
+  apsp_status st = apsp_batch_create(W, D, P, n, count, opt, &b, stream);
+  if (st != APSP_OK) return st;
+  st = apsp_batch_launch(b, stream);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && st == APSP_OK) st = APSP_ECUDA;
+  batch_free(b);
+  if (st == APSP_OK && bs_used)
+    for (int g = 0; g < count; ++g) bs_used[g] = kBBS;
+  return st;
+}

@@ -227,59 +227,48 @@ static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats*
   return APSP_OK;
 }
 
-apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
-                   size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
-  apsp_options o = opt ? *opt : default_options();
-  if (n < 1 || !W || !D || !P) return APSP_EINVAL;
-  if (o.bs == 0) o.bs = apsp_default_bs(n);
-  if (!valid_bs(o.bs)) return APSP_EINVAL;
-  if (o.dtype < APSP_DTYPE_AUTO || o.dtype > APSP_DTYPE_U16X2) return APSP_EINVAL;
-  if (!o.validate && o.dtype != APSP_DTYPE_F32) return APSP_EINVAL;
-  if (n > 65536) return APSP_EINVAL;
-
+size_t fw_exec_workspace(int n, int dtype) {
   Plan pl;
   pl.n = n;
   pl.n_pad = padded_order(n);
-  pl.bs = o.bs;
+  pl.dtype = dtype;
   const bool pad = pl.n_pad != n;
+  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad;
+  layout(pl, !pad);
+  return pl.ws_total;
+}
 
-  // Workspace: caller's, or stream-ordered allocation of the largest need.
+// Run the block rounds with the arithmetic already chosen (no input scan).
+apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dtype, int flags, void* workspace,
+                    size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
+  Plan pl;
+  pl.n = n;
+  pl.n_pad = padded_order(n);
+  pl.bs = bs;
+  pl.dtype = dtype;
+  const bool pad = pl.n_pad != n;
+  const bool p_in_place = !pad && aligned16(P);
+  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad && aligned16(D);
+  layout(pl, p_in_place);
   void* ws = workspace;
   bool own_ws = false;
-  const size_t need_max = std::max<size_t>(apsp_fw_workspace_size(n, &o), 256);
   if (ws == nullptr) {
-    if (cudaMallocAsync(&ws, need_max, s) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, std::max<size_t>(pl.ws_total, 256), s) != cudaSuccess) {
       cudaGetLastError();
       return APSP_ENOMEM;
     }
     own_ws = true;
-    workspace_bytes = need_max;
+  } else if (workspace_bytes < pl.ws_total) {
+    return APSP_ENOMEM;
   }
-  if (((uintptr_t)ws & 255) != 0) return APSP_EINVAL;
-  auto fail = [&](apsp_status st) {
-    if (own_ws) cudaFreeAsync(ws, s);
-    return st;
-  };
-
-  int dtype = APSP_DTYPE_F32;
-  if (o.validate) {
-    if (workspace_bytes < sizeof(WeightStats)) return fail(APSP_ENOMEM);
-    apsp_status st = scan_and_choose(W, n, o.dtype, reinterpret_cast<WeightStats*>(ws), s, &dtype);
-    if (st != APSP_OK) return fail(st);
-  }
-  pl.dtype = dtype;
-  const bool p_in_place = !pad && aligned16(P);
-  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad && aligned16(D);
-  layout(pl, p_in_place);
-  if (workspace_bytes < pl.ws_total) return fail(APSP_ENOMEM);
 
   char* wsb = static_cast<char*>(ws);
   int32_t* Pw = p_in_place ? P : reinterpret_cast<int32_t*>(wsb + pl.ws_p);
   const size_t quads = (size_t)pl.n_pad * (pl.n_pad / 4);
   PhaseTimer tm;
   tm.s = s;
-  tm.on = (o.flags & APSP_FLAG_TIME_PHASES) != 0;
-  int aux = o.validate ? 1 : 0;
+  tm.on = (flags & APSP_FLAG_TIME_PHASES) != 0;
+  int aux = 0;
   cudaError_t e = cudaSuccess;
   if (dtype == APSP_DTYPE_F32) {
     float* Dw = pl.in_place ? D : reinterpret_cast<float*>(wsb + pl.ws_d);
@@ -314,13 +303,45 @@ apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_optio
     info->dtype_used = dtype;
     info->rounds = pl.n_pad / pl.bs;
     info->n_pad = pl.n_pad;
-    info->launches = aux + tm.launches[0] + tm.launches[1] + tm.launches[2];
+    info->launches += aux + tm.launches[0] + tm.launches[1] + tm.launches[2];
     for (int q = 0; q < 3; ++q) {
       info->phase_launches[q] = tm.launches[q];
       info->phase_ms[q] = ms[q];
     }
   }
   return APSP_OK;
+}
+
+apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
+                   size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
+  apsp_options o = opt ? *opt : default_options();
+  if (n < 1 || !W || !D || !P) return APSP_EINVAL;
+  if (o.bs == 0) o.bs = apsp_default_bs(n);
+  if (!valid_bs(o.bs)) return APSP_EINVAL;
+  if (o.dtype < APSP_DTYPE_AUTO || o.dtype > APSP_DTYPE_U16X2) return APSP_EINVAL;
+  if (!o.validate && o.dtype != APSP_DTYPE_F32) return APSP_EINVAL;
+  if (n > 65536) return APSP_EINVAL;
+  if (workspace && ((uintptr_t)workspace & 255) != 0) return APSP_EINVAL;
+  if (info) std::memset(info, 0, sizeof(*info));
+
+  // Scan counters: the caller's workspace head, or a small stream-ordered buffer.
+  int dtype = APSP_DTYPE_F32;
+  if (o.validate) {
+    void* sbuf = workspace;
+    if (sbuf == nullptr) {
+      if (cudaMallocAsync(&sbuf, 256, s) != cudaSuccess) {
+        cudaGetLastError();
+        return APSP_ENOMEM;
+      }
+    } else if (workspace_bytes < sizeof(WeightStats)) {
+      return APSP_ENOMEM;
+    }
+    apsp_status st = scan_and_choose(W, n, o.dtype, reinterpret_cast<WeightStats*>(sbuf), s, &dtype);
+    if (workspace == nullptr) cudaFreeAsync(sbuf, s);
+    if (st != APSP_OK) return st;
+    if (info) info->launches = 1;
+  }
+  return fw_exec(W, D, P, n, o.bs, dtype, o.flags, workspace, workspace_bytes, info, s);
 }
 
 }  // namespace apsp

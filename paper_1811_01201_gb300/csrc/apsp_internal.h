@@ -13,8 +13,34 @@ int sm_count();
 // n rounded up to the working tile order (a multiple of 128).
 int padded_order(int n);
 
+// Workspace bytes of fw_exec for a given arithmetic.
+size_t fw_exec_workspace(int n, int dtype);
+
+// Block rounds with the arithmetic already chosen (no input scan; async).
+// workspace may be NULL (stream-ordered allocation inside).
+apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dtype, int flags, void* workspace,
+                    size_t workspace_bytes, apsp_run_info* info, cudaStream_t s);
+
 // Single-graph run on device buffers (the body of apsp_fw_ex).
 apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_options* opt, void* workspace,
                    size_t workspace_bytes, apsp_run_info* info, cudaStream_t s);
+
+// Descriptor of one graph of an asynchronous batch (same layout as the
+// batched kernel's table entry).
+struct BatchGraphDesc {
+  const float* W;
+  float* D;
+  int32_t* P;
+  int n;
+  int pad;
+};
+
+// Largest graph order of the batched kernel.
+constexpr int kBatchMaxN = 512;
+
+// One-shot asynchronous batch launch for pre-validated graphs. host_graphs
+// points to `count` descriptors followed by `count` ints (the processing
+// order, largest first), all page-locked and alive until the stream passes.
+apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cudaStream_t s);
 
 }  // namespace apsp

@@ -62,3 +62,22 @@ def test_path_helper_matches_oracle_walk():
     bad = P.copy()
     bad[0, 1] = 0  # intermediate equal to an endpoint
     assert apsp.apsp_path(bad, 0, 1) is None
+
+
+def test_argument_checks_return_status_without_touching_the_gpu():
+    # every one of these is rejected by host-side validation before any CUDA call
+    L = apsp.load()
+    vp = ctypes.c_void_p
+    assert L.apsp_fw(None, None, None, 16, None) == apsp.APSP_EINVAL
+    o = apsp.apsp_options(48, 0, 1, 0)
+    assert L.apsp_fw_ex(None, None, None, 0, ctypes.byref(o), None, 0, None, None) == apsp.APSP_EINVAL
+    assert L.apsp_batch_create(None, None, None, None, 0, None, ctypes.byref(vp()), None) == apsp.APSP_EINVAL
+    assert L.apsp_batch_launch(None, None) == apsp.APSP_EINVAL
+    assert L.apsp_serve_create(None, 1 << 30, 4) == apsp.APSP_EINVAL
+    h = vp()
+    assert L.apsp_serve_create(ctypes.byref(h), 1 << 30, 0) == apsp.APSP_EINVAL
+    assert L.apsp_serve_submit(None, None, 10, None) == apsp.APSP_EINVAL
+    assert L.apsp_serve_poll(None, 1, None, None, None, 0) == apsp.APSP_EINVAL
+    assert L.apsp_serve_stats(None, None) == apsp.APSP_EINVAL
+    assert L.apsp_serve_destroy(None) == apsp.APSP_EINVAL
+    assert L.apsp_batched_bs(100) == 32
