@@ -312,10 +312,134 @@ def run_gpu(args, rank: int, world: int):
                        "ms_per_step": round(et * 1e3, 3), "steps": args.e2e_steps,
                        "api": "apsp_fw_host (pinned host buffers)"}
 
+    if args.batched:
+        line["batched"] = run_batched(args, dev)
+    if args.serve_seconds > 0:
+        line["served"] = run_serve(args, dev, args.serve_seconds)
+
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batched and served workloads
+
+def run_batched(args, dev, count=4096, seed=6) -> dict:
+    """4096 independent dense digraphs, n log-uniform in [16, 512], integer weights U[1,100],
+    density 0.7: one CUDA-graph-captured persistent launch vs one library call per graph."""
+    import torch
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+    ns = inputs.batch_sizes(count, seed)
+    Ws = [inputs.dense_digraph(n, inputs.batch_graph_seed(seed, g), 1, 100, density=0.7, device=dev)
+          for g, n in enumerate(ns)]
+    Ds = [torch.empty_like(w) for w in Ws]
+    Ps = [torch.empty(w.shape, dtype=torch.int32, device=dev) for w in Ws]
+    flops = sum(2.0 * n ** 3 for n in ns)
+    s = torch.cuda.Stream(device=dev)
+    b = apsp.Batch(Ws, Ds, Ps, stream=s)
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            b.launch(stream=s)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.launch(stream=s)
+    reps = max(3, args.steps)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) / reps * 1e-3
+    # one library call per graph (async, no validation): the per-graph launch path
+    with torch.cuda.stream(s):
+        for g in range(count):
+            apsp.apsp_fw_ex(Ws[g], Ds[g], Ps[g], bs=32, dtype=apsp.DTYPE_F32, validate=False, stream=s)
+    s.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for g in range(count):
+            apsp.apsp_fw_ex(Ws[g], Ds[g], Ps[g], bs=32, dtype=apsp.DTYPE_F32, validate=False, stream=s)
+    s.synchronize()
+    t_s = time.perf_counter() - t0
+    b.close()
+    return {"workload": f"{count} dense digraphs, n log-uniform [16,512], integer weights U[1,100], density 0.7",
+            "graphs_per_s": round(count / t_b, 1), "gflops": round(flops / t_b / 1e9, 1),
+            "ms_per_batch": round(t_b * 1e3, 3), "launch": "one persistent kernel replayed from a CUDA graph",
+            "per_graph_calls": {"graphs_per_s": round(count / t_s, 1), "gflops": round(flops / t_s / 1e9, 1),
+                                "ms": round(t_s * 1e3, 1)},
+            "speedup_vs_per_graph": round(t_s / t_b, 2)}
+
+
+def run_serve(args, dev, seconds: float, seed=7, pool_size=512) -> dict:
+    """Poisson stream of requests, n = clip(round(lognormal(ln 256, 1.0)), 32, 4096), integer
+    weights U[1,64]; arrival rate 80% of the measured saturation throughput."""
+    import numpy as np
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+    ns = inputs.lognormal_sizes(pool_size, seed)
+    pool = [inputs.dense_digraph(n, inputs.batch_graph_seed(seed, g), 1, 64).numpy() for g, n in enumerate(ns)]
+
+    def drive(srv, arrivals):
+        done = []
+        q = []
+        lock = threading.Lock()
+
+        def poller():
+            k = 0
+            while True:
+                with lock:
+                    item = q[k] if k < len(q) else None
+                if item is None:
+                    if len(done) >= len(arrivals):
+                        return
+                    time.sleep(0.0002)
+                    continue
+                jid, n = item
+                srv.poll(jid, n, timeout_ms=-1)
+                done.append(jid)
+                k += 1
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            W = pool[i % pool_size]
+            jid = srv.submit(W)
+            with lock:
+                q.append((jid, W.shape[0]))
+        th.join()
+        return time.perf_counter() - t0
+
+    budget = 100 << 30
+    with apsp.Server(budget, max_slots=256) as srv:   # saturation: everything at once
+        burst = [0.0] * 1024
+        el = drive(srv, burst)
+        sat = len(burst) / el
+    rate = 0.8 * sat
+    count = int(rate * seconds)
+    arrivals = inputs.poisson_arrivals(count, seed, rate)
+    with apsp.Server(budget, max_slots=256) as srv:
+        el = drive(srv, arrivals)
+        st = srv.stats()
+    flops = sum(2.0 * pool[i % pool_size].shape[0] ** 3 for i in range(count))
+    return {"workload": "Poisson requests, n=clip(round(lognormal(ln256,1)),32,4096), int weights U[1,64], "
+                        "100 GiB HBM budget; results copied to host on poll",
+            "seconds": round(el, 2), "requests": count, "arrival_rate_per_s": round(rate, 1),
+            "saturation_graphs_per_s": round(sat, 1), "graphs_per_s": round(st.completed / el, 1),
+            "gflops": round(flops / el / 1e9, 1), "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
+            "max_ms": round(st.max_ms, 3), "hbm_peak_gib": round(st.hbm_peak / 2 ** 30, 3)}
 
 
 def main():
@@ -331,8 +455,10 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-sample-n", type=int, default=1280)
-    ap.add_argument("--ref-sample-n", type=int, default=768)
+    ap.add_argument("--cpu-sample-n", type=int, default=2560)
+    ap.add_argument("--ref-sample-n", type=int, default=1536)
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
 

@@ -79,8 +79,12 @@ struct PhaseTimer {
 
 // ---------------------------------------------------------------- launch tables
 
+// First-wave stagger of the fp32 phase-3 launch (cycles; see the kernel).
+constexpr int kStaggerCycles = 6000;
+
 template <class T, int BS>
-static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pad, cudaStream_t s, PhaseTimer& tm) {
+static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pad, cudaStream_t s, PhaseTimer& tm,
+                                    RoundMax* rm, int graph_int) {
   const int R = n_pad / BS;
   const int nT = n_pad / kTile;
   const size_t ld = (size_t)n_pad;
@@ -98,15 +102,17 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
     attr_err = e1 != cudaSuccess ? e1 : e2;
   });
   if (attr_err != cudaSuccess) return attr_err;
+  RoundMax* rmx = std::is_same<T, F32T>::value ? rm : nullptr;
+  const int sms = sm_count();
   tm.mark(-1);
   for (int r = 0; r < R; ++r) {
-    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r);
+    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r, rmx);
     tm.mark(0);
     if (R > 1) {
-      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R);
+      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rmx);
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value)
-        fw_phase3_f32_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r);
+        fw_phase3_f32_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, kStaggerCycles, sms);
       else
         fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r);
       tm.mark(2);
@@ -117,11 +123,11 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
 
 template <class T>
 static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, int bs, cudaStream_t s,
-                                 PhaseTimer& tm) {
+                                 PhaseTimer& tm, RoundMax* rm, int graph_int) {
   switch (bs) {
-    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm);
-    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm);
-    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm);
+    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm, rm, graph_int);
+    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm, rm, graph_int);
+    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm, rm, graph_int);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -138,12 +144,14 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-// Workspace layout for a given arithmetic: [stats][D work][P work].
+// Workspace layout for a given arithmetic: [stats + round maxima][D work][P work].
+constexpr size_t kRoundMaxOffset = 64;  // RoundMax inside the 256-byte head
 static void layout(Plan& pl, bool p_in_place) {
   const size_t np2 = (size_t)pl.n_pad * pl.n_pad;
   size_t off = 0;
   pl.ws_stats = off;
-  off = align256(off + sizeof(WeightStats));
+  static_assert(sizeof(WeightStats) <= kRoundMaxOffset, "stats overlap the round maxima");
+  off = align256(off + kRoundMaxOffset + sizeof(RoundMax));
   pl.ws_d = off;
   if (pl.dtype == APSP_DTYPE_U16X2) off = align256(off + np2 * sizeof(uint16_t));
   else if (!pl.in_place) off = align256(off + np2 * sizeof(float));
@@ -212,7 +220,8 @@ extern "C" size_t apsp_fw_workspace_size(int n, const apsp_options* opt) {
 namespace apsp {
 
 // Scan W and decide the arithmetic. Synchronises `s` once.
-static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats* dstats, cudaStream_t s, int* dtype_out) {
+static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats* dstats, cudaStream_t s, int* dtype_out,
+                                   int* graph_int) {
   if (cudaMemsetAsync(dstats, 0, sizeof(WeightStats), s) != cudaSuccess) return APSP_ECUDA;
   scan_weights_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(W, n, dstats);
   WeightStats hs;
@@ -223,6 +232,7 @@ static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats*
   std::memcpy(&mx, &hs.max_bits, sizeof(mx));
   const bool eligible = hs.n_fraction == 0 && (double)mx * (double)(n - 1) < 65535.0;
   if (want == APSP_DTYPE_U16X2 && !eligible) return APSP_EINVAL;
+  *graph_int = hs.n_fraction == 0;
   *dtype_out = (want == APSP_DTYPE_F32) ? APSP_DTYPE_F32 : (eligible ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32);
   return APSP_OK;
 }
@@ -239,8 +249,8 @@ size_t fw_exec_workspace(int n, int dtype) {
 }
 
 // Run the block rounds with the arithmetic already chosen (no input scan).
-apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dtype, int flags, void* workspace,
-                    size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
+apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dtype, int graph_int, int flags,
+                    void* workspace, size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
   Plan pl;
   pl.n = n;
   pl.n_pad = padded_order(n);
@@ -274,7 +284,8 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     float* Dw = pl.in_place ? D : reinterpret_cast<float*>(wsb + pl.ws_d);
     init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
-    e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm);
+    e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset),
+                            graph_int);
     if (e == cudaSuccess && !pl.in_place) {
       copy_out_kernel<float><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;
@@ -283,7 +294,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     uint16_t* Dw = reinterpret_cast<uint16_t*>(wsb + pl.ws_d);
     init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
-    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm);
+    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, nullptr, 0);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;
@@ -326,6 +337,7 @@ apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_optio
 
   // Scan counters: the caller's workspace head, or a small stream-ordered buffer.
   int dtype = APSP_DTYPE_F32;
+  int graph_int = 0;  // unknown without the scan: phase 3 then takes the generic P search
   if (o.validate) {
     void* sbuf = workspace;
     if (sbuf == nullptr) {
@@ -336,12 +348,12 @@ apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_optio
     } else if (workspace_bytes < sizeof(WeightStats)) {
       return APSP_ENOMEM;
     }
-    apsp_status st = scan_and_choose(W, n, o.dtype, reinterpret_cast<WeightStats*>(sbuf), s, &dtype);
+    apsp_status st = scan_and_choose(W, n, o.dtype, reinterpret_cast<WeightStats*>(sbuf), s, &dtype, &graph_int);
     if (workspace == nullptr) cudaFreeAsync(sbuf, s);
     if (st != APSP_OK) return st;
     if (info) info->launches = 1;
   }
-  return fw_exec(W, D, P, n, o.bs, dtype, o.flags, workspace, workspace_bytes, info, s);
+  return fw_exec(W, D, P, n, o.bs, dtype, graph_int, o.flags, workspace, workspace_bytes, info, s);
 }
 
 }  // namespace apsp

@@ -88,6 +88,7 @@ struct Job {
   int bs = 32;
   int dtype = APSP_DTYPE_F32;
   bool small = true;
+  bool integral = false;
   size_t footprint = 0;
   float* hW = nullptr;
   float* hD = nullptr;
@@ -190,7 +191,7 @@ static void run_dispatch(ServerImpl* s, Dispatch* d) {
       status = batch_launch_async(tbl, count, st);
     } else {
       auto& j = d->jobs.front();
-      status = fw_exec(j->dD, j->dD, j->dP, j->n, j->bs, j->dtype, 0, nullptr, 0, nullptr, st);
+      status = fw_exec(j->dD, j->dD, j->dP, j->n, j->bs, j->dtype, j->integral ? 1 : 0, 0, nullptr, 0, nullptr, st);
     }
   }
   for (auto& j : d->jobs) {
@@ -356,6 +357,7 @@ extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n
   j->bs = j->small ? 32 : apsp_default_bs(n);
   const bool eligible = !frac && (double)mx * (double)(n - 1) < 65535.0;
   j->dtype = (!j->small && eligible) ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32;
+  j->integral = !frac;
   j->footprint = job_footprint(n, j->small, j->dtype);
   if (j->footprint > s.budget) {
     std::lock_guard<std::mutex> g(s.m);

@@ -44,6 +44,15 @@ struct U16T {
   static __device__ __forceinline__ reg_t add(reg_t a, reg_t b) { return min(a + b, kInf16); }
 };
 
+// Largest finite panel values of the current round (fp32 bit patterns; for
+// non-negative floats the integer order is the value order). Phase 1 resets
+// it and adds the diagonal block; phase 2 adds its column-panel blocks to `a`
+// (the A operand of phase 3) and its row-panel blocks to `b` (the B operand).
+struct RoundMax {
+  unsigned int a_bits;
+  unsigned int b_bits;
+};
+
 // Threads and per-thread sub-block of the sequential (phase 1 / phase 2) tile
 // routine: BS x BS tile, each thread owns TE x TE elements.
 template <int BS>

@@ -12,13 +12,14 @@
 // candidate equals D'. The kernel therefore runs the hot loop as one FADD and
 // one FMNMX per update and recovers P afterwards:
 //
-//  * integer-valued tile panels whose largest finite sum stays within a bound:
-//    every operand is scaled by M = 2*BS and the A panel carries k+1 in the
-//    low bits (A' = M*a + k + 1, B' = M*b, D' = M*d; k+1 <= BS < M). The
-//    candidate keys M*(a+b) + k + 1 are exact while below 2^24, so min over
-//    keys yields the minimum value and, among equal values, the smallest k --
-//    while the old D (slot 0) wins ties, as the strict '<' requires. P comes
-//    for free.
+//  * integer-valued graphs whose round panels' largest finite values sum to
+//    at most a bound (phases 1-2 record the maxima): every operand is scaled
+//    by M = 2*BS and the A panel carries k+1 in the low bits (A' = M*a + k + 1,
+//    B' = M*b, D' = M*d; k+1 <= BS < M). The candidate keys M*(a+b) + k + 1
+//    are exact while below 2^24, so min over keys yields the minimum value
+//    and, among equal values, the smallest k -- while the old D (slot 0) wins
+//    ties, as the strict '<' requires. Slot 0 in the result means unchanged,
+//    so neither the old tile nor a search is needed: P comes for free.
 //  * otherwise (real-valued weights, large distances): improved elements are
 //    found by comparing with the old D, and each warp re-evaluates the BS
 //    candidates of one improved element at a time, one k per lane, taking
@@ -58,26 +59,18 @@ __device__ __forceinline__ int mp_col(int tx, int c) { return (c < 4) ? tx * 4 +
 
 __device__ __forceinline__ bool is_int_or_inf(float v) { return !(v < f32_inf()) || v == floorf(v); }
 
+__device__ __forceinline__ float floor_pos(float v) {
+  // floor for 0 <= v < 2^23 on the FMA pipe: round-down add of 2^23, then subtract
+  return __fsub_rn(__fadd_rd(v, 8388608.f), 8388608.f);
+}
+
 template <int BS>
-__global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
-                                                               size_t ld, int nT, int r) {
-  extern __shared__ __align__(16) float sm[];
-  float* As = sm;              // As[k * kSst + i] = D[r0 + i][kb + k]
-  float* Bs = sm + BS * kSst;  // Bs[k * kSst + j] = D[kb + k][c0 + j]
-  __shared__ int s_maxA, s_maxB, s_frac;
-
-  const int kb = r * BS;
-  const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
-  const int r0 = tr * kTile, c0 = tc * kTile;
-  // Tiles entirely inside row band r or column band r belong to phases 1-2.
-  if (r0 >= kb && r0 + kTile <= kb + BS) return;
-  if (c0 >= kb && c0 + kTile <= kb + BS) return;
-
+__device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __restrict__ P, size_t ld, int kb,
+                                          int r0, int c0, bool keyed, float* As, float* Bs) {
+  constexpr float M = KeyParams<BS>::M;
+  const float INF = f32_inf();
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) { s_maxA = 0; s_maxB = 0; s_frac = 0; }
-
-  // C tile -> registers (16 x 128-bit loads, coalesced along rows).
   float d[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -87,64 +80,34 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
     d[a][0] = v0.x; d[a][1] = v0.y; d[a][2] = v0.z; d[a][3] = v0.w;
     d[a][4] = v1.x; d[a][5] = v1.y; d[a][6] = v1.z; d[a][7] = v1.w;
   }
-
-  // B panel slice: BS rows x 128 columns, 128-bit loads and stores.
-  float mxb = 0.f, mxa = 0.f;
-  bool frac = false;
+  const float mb = keyed ? M : 1.f;
 #pragma unroll
   for (int m = 0; m < BS / 8; ++m) {
     const int idx = tid + 256 * m, k = idx >> 5, q = idx & 31;
-    const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(kb + k) * ld + c0 + q * 4);
+    float4 v = *reinterpret_cast<const float4*>(D + (size_t)(kb + k) * ld + c0 + q * 4);
+    v.x *= mb; v.y *= mb; v.z *= mb; v.w *= mb;
     *reinterpret_cast<float4*>(Bs + k * kSst + q * 4) = v;
-    mxb = fmaxf(mxb, fmaxf(fmaxf(v.x < f32_inf() ? v.x : 0.f, v.y < f32_inf() ? v.y : 0.f),
-                           fmaxf(v.z < f32_inf() ? v.z : 0.f, v.w < f32_inf() ? v.w : 0.f)));
-    frac |= !(is_int_or_inf(v.x) && is_int_or_inf(v.y) && is_int_or_inf(v.z) && is_int_or_inf(v.w));
   }
-  // A panel slice: 128 rows x BS columns, stored transposed. Lane -> (row
-  // ri = lane & 7 of an 8-row group, column quad cq = lane >> 3).
 #pragma unroll
   for (int m = 0; m < BS / 8; ++m) {
     const int idx = tid + 256 * m;
-    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;  // grp: 0 .. 4*BS/8-1
-    const int rows_per_pass = 8;
-    const int quads = BS / 4;
-    const int i = (grp % (kTile / rows_per_pass)) * rows_per_pass + ri;
-    const int q4 = (grp / (kTile / rows_per_pass)) * 4 + cq;
-    if (q4 < quads) {
-      const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
-      As[(q4 * 4 + 0) * kSst + i] = v.x;
-      As[(q4 * 4 + 1) * kSst + i] = v.y;
-      As[(q4 * 4 + 2) * kSst + i] = v.z;
-      As[(q4 * 4 + 3) * kSst + i] = v.w;
-      mxa = fmaxf(mxa, fmaxf(fmaxf(v.x < f32_inf() ? v.x : 0.f, v.y < f32_inf() ? v.y : 0.f),
-                             fmaxf(v.z < f32_inf() ? v.z : 0.f, v.w < f32_inf() ? v.w : 0.f)));
-      frac |= !(is_int_or_inf(v.x) && is_int_or_inf(v.y) && is_int_or_inf(v.z) && is_int_or_inf(v.w));
-    }
+    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
+    const int i = (grp % (kTile / 8)) * 8 + ri;
+    const int q4 = (grp / (kTile / 8)) * 4 + cq;
+    const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
+    const float add0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
+    As[(q4 * 4 + 0) * kSst + i] = fmaf(v.x, mb, add0);
+    As[(q4 * 4 + 1) * kSst + i] = fmaf(v.y, mb, keyed ? add0 + 1.f : 0.f);
+    As[(q4 * 4 + 2) * kSst + i] = fmaf(v.z, mb, keyed ? add0 + 2.f : 0.f);
+    As[(q4 * 4 + 3) * kSst + i] = fmaf(v.w, mb, keyed ? add0 + 3.f : 0.f);
   }
-  __syncthreads();  // s_* initialised
-  atomicMax(&s_maxA, __float_as_int(mxa));
-  atomicMax(&s_maxB, __float_as_int(mxb));
-  if (frac) s_frac = 1;
-  __syncthreads();
-  constexpr float M = KeyParams<BS>::M;
-  const bool keyed =
-      (s_frac == 0) && (__int_as_float(s_maxA) + __int_as_float(s_maxB) <= KeyParams<BS>::bound);
-
   if (keyed) {
-    // A' = M a + (k + 1), B' = M b, D' = M d (all exact).
-    for (int t = tid; t < BS * kTile; t += 256) {
-      const int k = t / kTile, i = t - k * kTile;
-      As[k * kSst + i] = fmaf(As[k * kSst + i], M, (float)(k + 1));
-      Bs[k * kSst + i] = Bs[k * kSst + i] * M;
-    }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int c = 0; c < 8; ++c) d[a][c] *= M;
-    __syncthreads();
   }
-
-  // Hot loop: 64 independent FADD + FMNMX chains per thread per k.
+  __syncthreads();
   const float* Ap = As + ty * 4;
   const float* Bp = Bs + tx * 4;
 #pragma unroll 4
@@ -160,9 +123,38 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
 #pragma unroll
       for (int c = 0; c < 8; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
   }
-
-  // Epilogue: compare with the old tile (re-read; still in L2), write back
-  // only changed 4-element groups, never rows/columns of block r.
+  if (keyed) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int gi = r0 + mp_row(ty, a);
+      const bool band_r = (gi >= kb) && (gi < kb + BS);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gj = c0 + mp_col(tx, 4 * h);
+        const bool band_c = (gj >= kb) && (gj < kb + BS);
+        float nv[4];
+        int sl[4];
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float key = d[a][4 * h + e];
+          const bool fin = key < INF;
+          const float v = floor_pos(key * (1.f / M));
+          sl[e] = fin ? (int)__fmaf_rn(-v, M, key) : 0;
+          nv[e] = fin ? v : INF;
+          any |= sl[e] != 0;
+        }
+        if (any && !band_r && !band_c) {
+          float* dp = D + (size_t)gi * ld + gj;
+          *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (sl[e] != 0) P[(size_t)gi * ld + gj + e] = kb + sl[e] - 1;
+        }
+      }
+    }
+    return;
+  }
   uint64_t imp = 0;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -181,31 +173,14 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float dn = d[a][4 * h + e];
-        if (keyed) {
-          const bool im = dn < old[e] * M;
-          if (im) {
-            const float v = floorf(dn * (1.f / M));
-            const int s = (int)(dn - v * M);
-            nv[e] = v;
-            P[(size_t)gi * ld + gj + e] = kb + s - 1;
-          } else {
-            nv[e] = old[e];
-          }
-          any |= im;
-        } else {
-          const bool im = dn < old[e];
-          nv[e] = im ? dn : old[e];
-          if (im) imp |= 1ull << (a * 8 + 4 * h + e);
-          any |= im;
-        }
+        const bool im = dn < old[e];
+        nv[e] = im ? dn : old[e];
+        if (im) imp |= 1ull << (a * 8 + 4 * h + e);
+        any |= im;
       }
       if (any) *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
     }
   }
-  if (keyed) return;
-
-  // Generic path: recover P for each improved element, one warp per element,
-  // one candidate k per lane.
   if (!__any_sync(0xffffffffu, imp != 0)) return;
 #pragma unroll
   for (int slot = 0; slot < 64; ++slot) {
@@ -230,6 +205,34 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
       if (lane == src) P[(size_t)(r0 + li) * ld + c0 + lj] = kb + kstar;
     }
   }
+}
+
+__device__ __forceinline__ void spin_cycles(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+
+// One launch per round; one CTA per 128x128 tile, two CTAs per SM.
+//   rm:        the round's panel maxima written by phases 1-2
+//   graph_int: every weight of the graph is an integer (so every D value is)
+//   stagger:   CTAs sms .. 2*sms-1 (the first wave's second half) start this
+//              many cycles late, so the first wave's SMs do not all load their
+//              tiles from HBM at the same instant
+template <int BS>
+__global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
+                                                               size_t ld, int nT, int r, const RoundMax* __restrict__ rm,
+                                                               int graph_int, int stagger, int sms) {
+  extern __shared__ __align__(16) float sm[];
+  const int kb = r * BS;
+  const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
+  const int r0 = tr * kTile, c0 = tc * kTile;
+  // Tiles entirely inside row band r or column band r belong to phases 1-2.
+  if ((r0 >= kb && r0 + kTile <= kb + BS) || (c0 >= kb && c0 + kTile <= kb + BS)) return;
+  const bool keyed = graph_int != 0 &&
+                     __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
+  if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
+  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, sm, sm + BS * kSst);
 }
 
 }  // namespace apsp

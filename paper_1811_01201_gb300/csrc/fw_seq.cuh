@@ -16,6 +16,8 @@
 // in shared memory.
 #pragma once
 
+#include <type_traits>
+
 #include "fw_common.cuh"
 
 namespace apsp {
@@ -32,7 +34,7 @@ enum SeqMode { kSeqDiag = 0, kSeqRow = 1, kSeqCol = 2 };
 template <class T, int BS, int MODE>
 __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, int32_t* __restrict__ P, size_t ld,
                                          int kb, int ti0, int tj0, const typename T::reg_t* __restrict__ diag_s,
-                                         typename T::reg_t* rowbuf, typename T::reg_t* colbuf) {
+                                         typename T::reg_t* rowbuf, typename T::reg_t* colbuf, RoundMax* rm) {
   using S = SeqShape<BS>;
   using reg_t = typename T::reg_t;
   constexpr int TE = S::TE, TPR = S::TPR, DS = BS + 1;
@@ -92,22 +94,42 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
         P[off] = p[a][c];
       }
     }
+  if constexpr (std::is_same<T, F32T>::value) {
+    if (rm != nullptr) {
+      // largest finite value of the finished tile, for phase 3's exact-key test
+      unsigned mx = 0;
+#pragma unroll
+      for (int a = 0; a < TE; ++a)
+#pragma unroll
+        for (int c = 0; c < TE; ++c)
+          if (d[a][c] < f32_inf()) mx = max(mx, (unsigned)__float_as_int(d[a][c]));
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if ((threadIdx.x & 31) == 0) {
+        if (MODE != kSeqRow) atomicMax(&rm->a_bits, mx);
+        if (MODE != kSeqCol) atomicMax(&rm->b_bits, mx);
+      }
+    }
+  }
 }
 
 // Phase 1: the diagonal block of round r (one CTA).
 template <class T, int BS>
 __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase1_kernel(typename T::store_t* D, int32_t* P, size_t ld,
-                                                                     int r) {
+                                                                     int r, RoundMax* rm) {
   __shared__ typename T::reg_t rowbuf[2 * BS], colbuf[2 * BS];
   const int kb = r * BS;
-  seq_tile<T, BS, kSeqDiag>(D, P, ld, kb, kb, kb, nullptr, rowbuf, colbuf);
+  if (rm != nullptr && threadIdx.x == 0) {
+    rm->a_bits = 0;  // visible to this CTA's atomics after seq_tile's barriers
+    rm->b_bits = 0;
+  }
+  seq_tile<T, BS, kSeqDiag>(D, P, ld, kb, kb, kb, nullptr, rowbuf, colbuf, rm);
 }
 
 // Phase 2: the other blocks of row r (CTAs 0 .. R-2) and of column r
 // (CTAs R-1 .. 2R-3), all against the finished diagonal block.
 template <class T, int BS>
 __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase2_kernel(typename T::store_t* D, int32_t* P, size_t ld,
-                                                                     int r, int R) {
+                                                                     int r, int R, RoundMax* rm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using reg_t = typename T::reg_t;
   constexpr int DS = BS + 1;
@@ -123,11 +145,11 @@ __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase2_kernel(typename T:
   const int b = blockIdx.x;
   if (b < R - 1) {
     const int J = b < r ? b : b + 1;
-    seq_tile<T, BS, kSeqRow>(D, P, ld, kb, kb, J * BS, diag_s, rowbuf, colbuf);
+    seq_tile<T, BS, kSeqRow>(D, P, ld, kb, kb, J * BS, diag_s, rowbuf, colbuf, rm);
   } else {
     const int bb = b - (R - 1);
     const int I = bb < r ? bb : bb + 1;
-    seq_tile<T, BS, kSeqCol>(D, P, ld, kb, I * BS, kb, diag_s, rowbuf, colbuf);
+    seq_tile<T, BS, kSeqCol>(D, P, ld, kb, I * BS, kb, diag_s, rowbuf, colbuf, rm);
   }
 }
 
