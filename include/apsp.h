@@ -232,6 +232,39 @@ apsp_status apsp_serve_stats(apsp_server* s, apsp_stats* out);
 /* Cancel queued jobs, drain the device, join the scheduler, free everything. */
 apsp_status apsp_serve_destroy(apsp_server* s);
 
+/* ---------------------------------------------------------------- allocation-free solve */
+
+/*
+ * apsp_fw_noalloc: the single-graph solve of apsp_fw_ex without any device
+ * memory allocation. The paper has no counterpart; this exists for callers
+ * that cannot allocate device memory when they need a solve (a host framework
+ * that owns all device memory, code that must not block on or fail in an
+ * allocator mid-run, environments without the stream-ordered allocator).
+ * Its workspace is one fixed array of APSP_NOALLOC_SCRATCH_BYTES in device
+ * memory, part of the library and held by every GPU that loads it until the
+ * process exits.
+ *   W, D, P, n, opt, info, stream: as apsp_fw_ex (W, D, P device pointers the
+ *     caller owns; opt NULL = defaults). APSP_FLAG_TIME_PHASES is rejected
+ *     (APSP_EINVAL) because it would create CUDA events.
+ *   Limit: apsp_fw_workspace_size(n, opt) must not exceed
+ *     APSP_NOALLOC_SCRATCH_BYTES, else APSP_ENOMEM and nothing is enqueued.
+ *     With dtype F32 that allows any n that is a multiple of 128 and any
+ *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5760 when n
+ *     is a multiple of 128 (room for the 16-bit working matrix).
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any CUDA
+ *   stream capture.
+ *   All calls on a device share the array: calls that overlap on the GPU race
+ *   and corrupt each other. Nothing carries over between calls; each call
+ *   zeroes or rewrites what it uses.
+ */
+#define APSP_NOALLOC_SCRATCH_BYTES (64u << 20)
+apsp_status apsp_fw_noalloc(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
+                            apsp_run_info* info, void* stream);
+
+/* Size of the fixed array apsp_fw_noalloc works in (APSP_NOALLOC_SCRATCH_BYTES). */
+size_t apsp_noalloc_scratch_bytes(void);
+
 /* ---------------------------------------------------------------- host helpers */
 
 /*

@@ -111,6 +111,12 @@ def load(build_if_missing: bool = True):
         L.apsp_batch_launch.restype = c_int
         L.apsp_batch_destroy.argtypes = [vp]
         L.apsp_batch_destroy.restype = c_int
+    if hasattr(L, "apsp_fw_noalloc"):
+        L.apsp_fw_noalloc.argtypes = [vp, vp, vp, c_int, ctypes.POINTER(apsp_options),
+                                      ctypes.POINTER(apsp_run_info), vp]
+        L.apsp_fw_noalloc.restype = c_int
+        L.apsp_noalloc_scratch_bytes.argtypes = []
+        L.apsp_noalloc_scratch_bytes.restype = c_size
     if hasattr(L, "apsp_serve_create"):
         L.apsp_serve_create.argtypes = [ctypes.POINTER(vp), c_size, c_int]
         L.apsp_serve_create.restype = c_int
@@ -192,6 +198,20 @@ def apsp_fw_ex(W: torch.Tensor, D: torch.Tensor, P: torch.Tensor, bs: int = 0, d
     _check(load().apsp_fw_ex(_dev_ptr(W, torch.float32, n, "W"), _dev_ptr(D, torch.float32, n, "D"),
                              _dev_ptr(P, torch.int32, n, "P"), n, ctypes.byref(o), ws_ptr, ws_bytes,
                              ctypes.byref(info), _stream_ptr(stream)), "apsp_fw_ex")
+    return info
+
+
+def apsp_fw_noalloc(W: torch.Tensor, D: torch.Tensor, P: torch.Tensor, bs: int = 0, dtype: int = DTYPE_AUTO,
+                    validate: bool = True, stream=None) -> apsp_run_info:
+    """apsp_fw_noalloc: the solve of apsp_fw_ex without any device allocation, for callers that
+    cannot allocate device memory at the call site. It works in a fixed device array inside the
+    library (apsp_noalloc_scratch_bytes()); calls that overlap on the GPU share it and race."""
+    n = int(W.shape[0])
+    o = _opts(bs, dtype, validate)
+    info = apsp_run_info()
+    _check(load().apsp_fw_noalloc(_dev_ptr(W, torch.float32, n, "W"), _dev_ptr(D, torch.float32, n, "D"),
+                                  _dev_ptr(P, torch.int32, n, "P"), n, ctypes.byref(o), ctypes.byref(info),
+                                  _stream_ptr(stream)), "apsp_fw_noalloc")
     return info
 
 
