@@ -48,7 +48,8 @@ SM_MAX_MHZ = 2070.0
 ALU_PEAK_F32_TFLOPS = 2 * SMS * 64 * SM_MAX_MHZ * 1e6 / 1e12      # 40.27
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "phase3_f32_n32768_bs64.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "phase3_f32_n8192_bs64.md")
+PROFILE_N, PROFILE_BS = 8192, 64  # workload of that capture
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_01201_gb300", "csrc", "fw_minplus_f32.cuh")
 
 
@@ -111,9 +112,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile():
-    """Per-launch DRAM bytes of the phase-3 kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel source changed since."""
+def _traffic_from_profile(n: int, bs: int):
+    """Per-launch DRAM bytes of the phase-3 kernel from the committed ncu summary (captured at
+    n=8192), scaled to this n by the tile count ((n-BS)^2), or None when the summary is missing,
+    the block size differs, or the kernel source changed since the capture."""
+    if bs != PROFILE_BS:
+        return None
     try:
         text = open(PROFILE_SUMMARY).read()
         src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
@@ -127,17 +131,17 @@ def _traffic_from_profile():
     if got.get("kernel_source_sha256_16") != src_hash:
         return None
     try:
-        return float(got["dram_bytes_per_launch"])
+        return float(got["dram_bytes_per_launch"]) * ((n - bs) / (PROFILE_N - PROFILE_BS)) ** 2
     except (KeyError, ValueError):
         return None
 
 
 # ---------------------------------------------------------------- CPU oracle legs
 
-def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: int):
+def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: int, kind: str = "int"):
     import oracle
     from paper_1811_01201_gb300 import inputs
-    W = inputs.dense_digraph(n_full, seed, lo, hi, rows=(0, n_sample))[:, :n_sample].contiguous().numpy()
+    W = inputs.dense_digraph(n_full, seed, lo, hi, kind=kind, rows=(0, n_sample))[:, :n_sample].contiguous().numpy()
     t0 = time.perf_counter()
     oracle.fw_blocked(W, bs)
     dt = time.perf_counter() - t0
@@ -145,7 +149,7 @@ def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: 
 
 
 def cpu_baseline(args) -> dict:
-    dt, flops = _oracle_sample(args.n, args.seed, 1, 1000, args.cpu_sample_n, args.bs)
+    dt, flops = _oracle_sample(args.n, args.seed, 1, 1000, args.cpu_sample_n, args.bs, args.kind)
     return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
             "sample": f"serial C blocked FW (BS={args.bs}) on the leading {args.cpu_sample_n}x{args.cpu_sample_n} "
                       f"block of the n={args.n} workload, {dt:.1f} s"}
@@ -157,11 +161,11 @@ def run_reference(args, rank: int, world: int):
     import oracle
     oracle.build()
     for _ in range(args.warmup):
-        _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs)
+        _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs, args.kind)
     times = []
     flops = 0.0
     for _ in range(args.steps):
-        dt, fl = _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs)
+        dt, fl = _oracle_sample(args.n, args.seed, 1, 1000, args.ref_sample_n, args.bs, args.kind)
         times.append(dt)
         flops = fl
     tot = sum(times)
@@ -180,9 +184,11 @@ def run_reference(args, rank: int, world: int):
 
 
 def _config(args) -> dict:
-    return {"workload": f"dense random digraph n={args.n}, fp32 integer weights U[1,1000], zero diagonal, "
+    wdesc = "fp32 integer weights U[1,1000]" if args.kind == "int" else "fp32 real weights U(0,1]"
+    return {"workload": f"dense random digraph n={args.n}, {wdesc}, zero diagonal, "
                         "int32 path matrix (blocked Floyd-Warshall, one full solve per step)",
-            "n": args.n, "bs": args.bs, "weights": "int [1,1000]", "density": 1.0,
+            "n": args.n, "bs": args.bs, "weights": "int [1,1000]" if args.kind == "int" else "real (0,1]",
+            "density": 1.0,
             "l2": "inputs larger than L2 (4 GiB D + 4 GiB P at n=32768); no flush"}
 
 
@@ -206,7 +212,7 @@ def run_gpu(args, rank: int, world: int):
         if world > 1:
             dist.barrier()
 
-    W = inputs.dense_digraph(n, args.seed, 1, 1000, device=dev)
+    W = inputs.dense_digraph(n, args.seed, 1, 1000, kind=args.kind, device=dev)
     D = torch.empty_like(W)
     P = torch.empty((n, n), dtype=torch.int32, device=dev)
     ws = torch.empty(apsp.apsp_fw_workspace_size(n, bs=args.bs, dtype=apsp.DTYPE_F32), dtype=torch.uint8,
@@ -257,7 +263,7 @@ def run_gpu(args, rank: int, world: int):
     roof = {"bound": "alu", "achieved": round(ph3_tflops, 3) if ph3_tflops else None,
             "peak": round(ALU_PEAK_F32_TFLOPS, 2), "unit": "TFLOP/s",
             "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
-            "traffic": _traffic_from_profile(),
+            "traffic": _traffic_from_profile(n, args.bs),
             "kernel": f"fw_phase3_f32_kernel<{args.bs}>",
             "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
             "phase_ms_per_step": [round(x / args.steps, 3) for x in ph_ms],
@@ -378,68 +384,78 @@ def run_batched(args, dev, count=4096, seed=6) -> dict:
             "speedup_vs_per_graph": round(t_s / t_b, 2)}
 
 
-def run_serve(args, dev, seconds: float, seed=7, pool_size=512) -> dict:
+def run_serve(args, dev, seconds: float, seed=7, pool_size=512, clients=4) -> dict:
     """Poisson stream of requests, n = clip(round(lognormal(ln 256, 1.0)), 32, 4096), integer
-    weights U[1,64]; arrival rate 80% of the measured saturation throughput."""
+    weights U[1,64]; arrival rate 80% of the measured saturation throughput. Requests come from
+    `clients` submitting threads (each a Poisson stream of rate/clients) and results are copied
+    back to host memory by as many polling threads."""
     import numpy as np
+    import torch
 
     import paper_1811_01201_gb300 as apsp
     from paper_1811_01201_gb300 import inputs
     ns = inputs.lognormal_sizes(pool_size, seed)
     pool = [inputs.dense_digraph(n, inputs.batch_graph_seed(seed, g), 1, 64).numpy() for g, n in enumerate(ns)]
 
-    def drive(srv, arrivals):
-        done = []
-        q = []
-        lock = threading.Lock()
+    def drive(srv, arrivals_per_client):
+        jobs = [[] for _ in range(clients)]
 
-        def poller():
+        def client(ci, arrivals):
+            t0 = start[0]
+            for i, ta in enumerate(arrivals):
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                W = pool[(ci * 7919 + i) % pool_size]
+                jobs[ci].append((srv.submit(W), W.shape[0]))
+
+        def poller(ci, total):
             k = 0
-            while True:
-                with lock:
-                    item = q[k] if k < len(q) else None
-                if item is None:
-                    if len(done) >= len(arrivals):
-                        return
+            while k < total:
+                if k >= len(jobs[ci]):
                     time.sleep(0.0002)
                     continue
-                jid, n = item
+                jid, n = jobs[ci][k]
                 srv.poll(jid, n, timeout_ms=-1)
-                done.append(jid)
                 k += 1
 
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.perf_counter()
-        for i, ta in enumerate(arrivals):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            W = pool[i % pool_size]
-            jid = srv.submit(W)
-            with lock:
-                q.append((jid, W.shape[0]))
-        th.join()
-        return time.perf_counter() - t0
+        start = [time.perf_counter()]
+        th = [threading.Thread(target=client, args=(c, arrivals_per_client[c])) for c in range(clients)]
+        th += [threading.Thread(target=poller, args=(c, len(arrivals_per_client[c]))) for c in range(clients)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return time.perf_counter() - start[0], sum(len(j) for j in jobs)
 
     budget = 100 << 30
-    with apsp.Server(budget, max_slots=256) as srv:   # saturation: everything at once
-        burst = [0.0] * 1024
-        el = drive(srv, burst)
-        sat = len(burst) / el
+    with apsp.Server(budget, max_slots=512) as srv:   # saturation: every request at time 0
+        el, cnt = drive(srv, [[0.0] * 256 for _ in range(clients)])
+        sat = cnt / el
     rate = 0.8 * sat
-    count = int(rate * seconds)
-    arrivals = inputs.poisson_arrivals(count, seed, rate)
-    with apsp.Server(budget, max_slots=256) as srv:
-        el = drive(srv, arrivals)
+    count = max(clients, int(rate * seconds))
+    per = count // clients
+    arr = [inputs.poisson_arrivals(per, seed * 100 + c, rate / clients) for c in range(clients)]
+    with apsp.Server(budget, max_slots=512) as srv:
+        el, cnt = drive(srv, arr)
         st = srv.stats()
-    flops = sum(2.0 * pool[i % pool_size].shape[0] ** 3 for i in range(count))
+    flops = sum(2.0 * pool[(c * 7919 + i) % pool_size].shape[0] ** 3 for c in range(clients) for i in range(per))
+    # the same request mix solved one at a time through the single-graph host call
+    seq_n = min(64, pool_size)
+    t0 = time.perf_counter()
+    for i in range(seq_n):
+        W = torch.from_numpy(pool[i])
+        n = W.shape[0]
+        apsp.apsp_fw_host(W, torch.empty((n, n)), torch.empty((n, n), dtype=torch.int32))
+    seq_gps = seq_n / (time.perf_counter() - t0)
     return {"workload": "Poisson requests, n=clip(round(lognormal(ln256,1)),32,4096), int weights U[1,64], "
-                        "100 GiB HBM budget; results copied to host on poll",
-            "seconds": round(el, 2), "requests": count, "arrival_rate_per_s": round(rate, 1),
-            "saturation_graphs_per_s": round(sat, 1), "graphs_per_s": round(st.completed / el, 1),
+                        f"100 GiB HBM budget, {clients} client threads; results copied to host on poll",
+            "seconds": round(el, 2), "requests": cnt, "arrival_rate_per_s": round(rate, 1),
+            "saturation_graphs_per_s": round(sat, 1), "graphs_per_s": round(cnt / el, 1),
             "gflops": round(flops / el / 1e9, 1), "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
-            "max_ms": round(st.max_ms, 3), "hbm_peak_gib": round(st.hbm_peak / 2 ** 30, 3)}
+            "max_ms": round(st.max_ms, 3), "hbm_peak_gib": round(st.hbm_peak / 2 ** 30, 3),
+            "one_at_a_time_graphs_per_s": round(seq_gps, 1),
+            "speedup_vs_one_at_a_time": round(sat / seq_gps, 2)}
 
 
 def main():
@@ -451,6 +467,8 @@ def main():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--bs", type=int, default=64)
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--kind", default="int", choices=["int", "real"],
+                    help="weights: integer U[1,1000] (default) or real U(0,1]")
     ap.add_argument("--no-u16", dest="u16", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=2)

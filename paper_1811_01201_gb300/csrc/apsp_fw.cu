@@ -102,19 +102,18 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
     attr_err = e1 != cudaSuccess ? e1 : e2;
   });
   if (attr_err != cudaSuccess) return attr_err;
-  RoundMax* rmx = std::is_same<T, F32T>::value ? rm : nullptr;
   const int sms = sm_count();
   tm.mark(-1);
   for (int r = 0; r < R; ++r) {
-    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r, rmx);
+    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r, rm);
     tm.mark(0);
     if (R > 1) {
-      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rmx);
+      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm);
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value)
         fw_phase3_f32_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, kStaggerCycles, sms);
       else
-        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r);
+        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, kStaggerCycles, sms);
       tm.mark(2);
     }
   }
@@ -294,7 +293,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     uint16_t* Dw = reinterpret_cast<uint16_t*>(wsb + pl.ws_d);
     init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
-    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, nullptr, 0);
+    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;

@@ -54,7 +54,7 @@ struct BatchQueue {
 };
 
 // Shared-memory layout (floats): diag[32][33], As[32][ldp], Bs[32][ldp]
-__host__ __device__ constexpr int batched_ldp(int n_max) { return ((n_max + 31) / 32) * 32 + 4; }
+__host__ __device__ constexpr int batched_ldp(int n_max) { return ((n_max + 31) / 32) * 32 + 8; }
 __host__ __device__ constexpr size_t batched_smem_bytes(int n_max) {
   return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * batched_ldp(n_max)) + 64;
 }
@@ -106,12 +106,15 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
         if (p1 >= 0 && j0 + 1 < kw) { D[(size_t)(kb + i) * n + kb + j0 + 1] = diag[i * 33 + j0 + 1]; P[(size_t)(kb + i) * n + kb + j0 + 1] = p1; }
       }
     }
-    // diagonal block entries of the panels (rows/cols in band r)
+    // diagonal block entries of the panels (rows/cols in band r); in key form
+    // the column panel carries slot k+1 and both are scaled by M
     for (int t = tid; t < 32 * 32; t += kBThreads) {
       const int k = t >> 5, x = t & 31;
       if (x < kw) {
-        As[k * ldp + kb + x] = diag[x * 33 + k];  // D[kb+x][kb+k]
-        Bs[k * ldp + kb + x] = diag[k * 33 + x];  // D[kb+k][kb+x]
+        const float av = diag[x * 33 + k];  // D[kb+x][kb+k]
+        const float bv = diag[k * 33 + x];  // D[kb+k][kb+x]
+        As[k * ldp + kb + x] = KEYED ? fmaf(av, kBKeyM, (float)(k + 1)) : av;
+        Bs[k * ldp + kb + x] = KEYED ? bv * kBKeyM : bv;
       }
     }
 
@@ -138,7 +141,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        Bs[lane * ldp + o] = valid ? x : INF;
+        Bs[lane * ldp + o] = valid ? (KEYED ? x * kBKeyM : x) : INF;
       }
       // column-panel row o: element t = D[o][kb+t]; c_t = x_k + Diag[k][t]
       for (int l = warp; l < nl; l += NW) {
@@ -152,37 +155,90 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        As[lane * ldp + o] = valid ? x : INF;
+        As[lane * ldp + o] = valid ? (KEYED ? fmaf(x, kBKeyM, (float)(lane + 1)) : x) : INF;
       }
     }
     __syncthreads();
 
     // ---------------- phase 3: every element outside band r
-    if (R > 1) {
-      if (KEYED) {
-        for (int t = tid; t < 32 * n; t += kBThreads) {
-          const int k = t / n, x = t - k * n;
-          As[k * ldp + x] = fmaf(As[k * ldp + x], kBKeyM, (float)(k + 1));
-          Bs[k * ldp + x] = Bs[k * ldp + x] * kBKeyM;
+    if (R > 1 && KEYED) {
+      // 16 x 32 threads, 8 x 4 elements each: 128 x 128 tiles; the next tile's
+      // elements are loaded while the current one computes
+      const int ty = tid >> 5, tx = lane;
+      const int tiles_c = (n + 127) / 128;
+      const int ntile = tiles_c * tiles_c;
+      float nxt[8][4];
+      auto load_tile = [&](int tile) {
+        const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
+        const int i0 = tr * 128 + ty * 8, j0 = tc * 128 + tx * 4;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = i0 + a, j = j0 + c;
+            nxt[a][c] = (i < n && j < n) ? D[(size_t)i * n + j] : INF;
+          }
+      };
+      load_tile(0);
+      for (int tile = 0; tile < ntile; ++tile) {
+        const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
+        const int i0 = tr * 128 + ty * 8, j0 = tc * 128 + tx * 4;
+        float d[8][4];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) d[a][c] = nxt[a][c] * kBKeyM;
+        if (tile + 1 < ntile) load_tile(tile + 1);
+        if (i0 < n && j0 < n) {
+          const float* Ap = As + i0;
+          const float* Bp = Bs + j0;
+#pragma unroll 8
+          for (int k = 0; k < kBBS; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
+            const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * ldp + 4);
+            const float4 b4 = *reinterpret_cast<const float4*>(Bp + k * ldp);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
+          }
+          // slot 0 = unchanged; slot s = improved at k = s-1
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int i = i0 + a, j = j0 + c;
+              const float key = d[a][c];
+              if (i >= n || j >= n || !(key < INF)) continue;
+              if ((i >= kb && i < kb + kw) || (j >= kb && j < kb + kw)) continue;
+              const float v = floorf(key * (1.f / kBKeyM));
+              const int sl = (int)(key - v * kBKeyM);
+              if (sl != 0) {
+                D[(size_t)i * n + j] = v;
+                P[(size_t)i * n + j] = kb + sl - 1;
+              }
+            }
         }
-        __syncthreads();
       }
+    } else if (R > 1) {
       const int ty = tid >> 5, tx = lane;  // 16 x 32 threads, 4 x 4 elements each: 64 x 128 tile
       const int tiles_r = (n + 63) / 64, tiles_c = (n + 127) / 128;
       for (int tile = 0; tile < tiles_r * tiles_c; ++tile) {
         const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
         const int i0 = tr * 64 + ty * 4, j0 = tc * 128 + tx * 4;
-        // skip groups entirely outside the graph
         const bool any_row = i0 < n, any_col = j0 < n;
-        float d[4][4], old[4][4];
+        float d[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int i = i0 + a, j = j0 + c;
-            old[a][c] = (i < n && j < n) ? D[(size_t)i * n + j] : INF;
-            d[a][c] = KEYED ? old[a][c] * kBKeyM : old[a][c];
+            d[a][c] = (i < n && j < n) ? D[(size_t)i * n + j] : INF;
           }
+        const float old[4][4] = {{d[0][0], d[0][1], d[0][2], d[0][3]}, {d[1][0], d[1][1], d[1][2], d[1][3]},
+                                 {d[2][0], d[2][1], d[2][2], d[2][3]}, {d[3][0], d[3][1], d[3][2], d[3][3]}};
         if (any_row && any_col) {
           const float* Ap = As + i0;
           const float* Bp = Bs + j0;
@@ -205,20 +261,12 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           for (int c = 0; c < 4; ++c) {
             const int i = i0 + a, j = j0 + c;
             const bool inside = i < n && j < n && !(i >= kb && i < kb + kw) && !(j >= kb && j < kb + kw);
-            if (!inside) continue;
-            if (KEYED) {
-              if (d[a][c] < old[a][c] * kBKeyM) {
-                const float v = floorf(d[a][c] * (1.f / kBKeyM));
-                const int s = (int)(d[a][c] - v * kBKeyM);
-                D[(size_t)i * n + j] = v;
-                P[(size_t)i * n + j] = kb + s - 1;
-              }
-            } else if (d[a][c] < old[a][c]) {
+            if (inside && d[a][c] < old[a][c]) {
               D[(size_t)i * n + j] = d[a][c];
               imp |= 1u << (a * 4 + c);
             }
           }
-        if (!KEYED && __any_sync(0xffffffffu, imp != 0)) {
+        if (__any_sync(0xffffffffu, imp != 0)) {
 #pragma unroll
           for (int slot = 0; slot < 16; ++slot) {
             unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);

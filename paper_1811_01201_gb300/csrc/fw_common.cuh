@@ -44,10 +44,11 @@ struct U16T {
   static __device__ __forceinline__ reg_t add(reg_t a, reg_t b) { return min(a + b, kInf16); }
 };
 
-// Largest finite panel values of the current round (fp32 bit patterns; for
-// non-negative floats the integer order is the value order). Phase 1 resets
-// it and adds the diagonal block; phase 2 adds its column-panel blocks to `a`
-// (the A operand of phase 3) and its row-panel blocks to `b` (the B operand).
+// Largest panel values of the current round. Phase 1 resets it and adds the
+// diagonal block; phase 2 adds its column-panel blocks to `a` (the A operand
+// of phase 3) and its row-panel blocks to `b` (the B operand). fp32: largest
+// finite value as a bit pattern (for non-negative floats the integer order is
+// the value order). 16-bit: largest value with INF (0xFFFF) included.
 struct RoundMax {
   unsigned int a_bits;
   unsigned int b_bits;

@@ -8,14 +8,15 @@
 // matter, and D and P come out bit-identical to the fp32 path.
 //
 // The hot loop is PTX add.u16x2 + min.u16x2: two updates per instruction
-// pair. A wrapping add is exact when no a + b in the tile can exceed 0xFFFF,
-// which the kernel checks per tile from the panel maxima; tiles that could
-// overflow (typically panels still holding INF) use the saturating form
-// sat(a + b) = min(a, ~b) + b (one more min per pair).
+// pair. A wrapping add is exact when no a + b can exceed 0xFFFF, which holds
+// when the round's panel maxima (recorded by phases 1-2, INF included) sum to
+// at most 0xFFFF; otherwise (typically while panels still hold INF) the round
+// uses the saturating form sat(a + b) = min(a, ~b) + b (one more min per pair).
 //
 // P is recovered as in the fp32 generic path: an element improved iff its new
-// value is below the old one; a warp then re-evaluates its BS candidates, one
-// k per lane, and takes the first k whose saturated sum equals the new value.
+// value is below the old one (kept in registers); a warp then re-evaluates its
+// BS candidates, one k per lane, and takes the first k whose saturated sum
+// equals the new value.
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads; each thread owns 8
 // rows (ty*4+{0..3}, 64+ty*4+{0..3}) x 8 consecutive columns (tx*8 ..), i.e.
@@ -78,37 +79,44 @@ __device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint
 
 template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restrict__ D, int32_t* __restrict__ P,
-                                                               size_t ld, int nT, int r) {
+                                                               size_t ld, int nT, int r,
+                                                               const RoundMax* __restrict__ rm, int stagger,
+                                                               int sms) {
   extern __shared__ __align__(16) uint32_t smu[];
   uint32_t* As = smu;                 // As[k * kSstA16 + i] = dup(D[r0 + i][kb + k])
   uint32_t* Bs = smu + BS * kSstA16;  // Bs[k * kSstB16 + q] = D[kb + k][c0 + 2q .. 2q+1]
-  __shared__ unsigned s_ma, s_mb;
 
   const int kb = r * BS;
   const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
   const int r0 = tr * kTile, c0 = tc * kTile;
   if (r0 >= kb && r0 + kTile <= kb + BS) return;
   if (c0 >= kb && c0 + kTile <= kb + BS) return;
+  // the round's panel maxima (INF included) decide whether a wrapping add is safe
+  const bool sat = rm->a_bits + rm->b_bits > 0xFFFFu;
+  if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < stagger) {
+    }
+  }
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) { s_ma = 0; s_mb = 0; }
 
-  uint32_t w[8][4];
+  uint32_t w[8][4], old[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(r0 + mp_row(ty, a)) * ld + c0 + tx * 8);
-    w[a][0] = v.x; w[a][1] = v.y; w[a][2] = v.z; w[a][3] = v.w;
+    old[a][0] = v.x; old[a][1] = v.y; old[a][2] = v.z; old[a][3] = v.w;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[a][q] = old[a][q];
   }
 
-  uint32_t mxa = 0, mxb = 0;
   // B slice: BS rows x 128 uint16 = 16 uint4 per row.
 #pragma unroll
   for (int m = 0; m < BS / 16; ++m) {
     const int idx = tid + 256 * m, k = idx >> 4, q = idx & 15;
     const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
     *reinterpret_cast<uint4*>(Bs + k * kSstB16 + q * 4) = v;
-    mxb = max(mxb, umax4(v));
   }
   // A slice: 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
 #pragma unroll
@@ -125,13 +133,8 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
       As[(q8 * 8 + 2 * e) * kSstA16 + i] = lo | (lo << 16);
       As[(q8 * 8 + 2 * e + 1) * kSstA16 + i] = hi | (hi << 16);
     }
-    mxa = max(mxa, umax4(v));
   }
-  __syncthreads();  // s_ma / s_mb initialised
-  atomicMax(&s_ma, mxa);
-  atomicMax(&s_mb, mxb);
   __syncthreads();
-  const bool sat = (s_ma + s_mb) > 0xFFFFu;
 
   if (sat)
     minplus_u16_loop<BS, true>(w, As + ty * 4, Bs + tx * 4);
@@ -147,17 +150,12 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
     const int gj = c0 + tx * 8;
     if ((gi >= kb && gi < kb + BS) || (gj >= kb && gj < kb + BS)) continue;
     uint16_t* dp = D + (size_t)gi * ld + gj;
-    const uint4 o4 = *reinterpret_cast<const uint4*>(dp);
-    const uint32_t old[4] = {o4.x, o4.y, o4.z, o4.w};
-    uint32_t nv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint32_t mn = vmin16(w[a][q], old[q]);  // never above old
-      nv[q] = mn;
-      if ((mn & 0xFFFF) < (old[q] & 0xFFFF)) imp |= 1ull << (a * 8 + 2 * q);
-      if ((mn >> 16) < (old[q] >> 16)) imp |= 1ull << (a * 8 + 2 * q + 1);
+      if ((w[a][q] & 0xFFFF) < (old[a][q] & 0xFFFF)) imp |= 1ull << (a * 8 + 2 * q);
+      if ((w[a][q] >> 16) < (old[a][q] >> 16)) imp |= 1ull << (a * 8 + 2 * q + 1);
     }
-    if (imp >> (a * 8) & 0xFF) *reinterpret_cast<uint4*>(dp) = make_uint4(nv[0], nv[1], nv[2], nv[3]);
+    if ((imp >> (a * 8)) & 0xFF) *reinterpret_cast<uint4*>(dp) = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
   }
 
   if (!__any_sync(0xffffffffu, imp != 0)) return;

@@ -94,20 +94,25 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
         P[off] = p[a][c];
       }
     }
-  if constexpr (std::is_same<T, F32T>::value) {
-    if (rm != nullptr) {
-      // largest finite value of the finished tile, for phase 3's exact-key test
-      unsigned mx = 0;
+  if (rm != nullptr) {
+    // Largest value of the finished tile for phase 3's per-round choice: fp32
+    // takes the largest finite value (bit pattern) for the exact-key bound;
+    // 16-bit takes the largest value including INF for the overflow test.
+    unsigned mx = 0;
 #pragma unroll
-      for (int a = 0; a < TE; ++a)
+    for (int a = 0; a < TE; ++a)
 #pragma unroll
-        for (int c = 0; c < TE; ++c)
+      for (int c = 0; c < TE; ++c) {
+        if constexpr (std::is_same<T, F32T>::value) {
           if (d[a][c] < f32_inf()) mx = max(mx, (unsigned)__float_as_int(d[a][c]));
-      mx = __reduce_max_sync(0xffffffffu, mx);
-      if ((threadIdx.x & 31) == 0) {
-        if (MODE != kSeqRow) atomicMax(&rm->a_bits, mx);
-        if (MODE != kSeqCol) atomicMax(&rm->b_bits, mx);
+        } else {
+          mx = max(mx, (unsigned)d[a][c]);
+        }
       }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) {
+      if (MODE != kSeqRow) atomicMax(&rm->a_bits, mx);
+      if (MODE != kSeqCol) atomicMax(&rm->b_bits, mx);
     }
   }
 }
