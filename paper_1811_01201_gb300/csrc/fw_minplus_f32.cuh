@@ -21,10 +21,11 @@
 //    ties, as the strict '<' requires. Slot 0 in the result means unchanged,
 //    so neither the old tile nor a search is needed: P comes for free.
 //  * otherwise (real-valued weights, large distances): improved elements are
-//    found by comparing with the old D, and each warp re-evaluates the BS
-//    candidates of one improved element at a time, one k per lane, taking
-//    the first lane whose sum equals D' (bit-identical FADD, so equality is
-//    exact).
+//    found by comparing with the old D. Where few improved, each warp
+//    re-evaluates the BS candidates of one improved element at a time, one k
+//    per lane, taking the first lane whose sum equals D'; where many improved
+//    (early rounds), every lane re-scans its own elements with k descending.
+//    Both use the bit-identical FADD, so equality is exact.
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads, 8 x 8 elements per
 // thread in registers (rows ty*4+{0..3}, 64+ty*4+{0..3}; columns likewise
@@ -39,6 +40,7 @@
 namespace apsp {
 
 constexpr int kSst = kTile + 4;  // shared row stride (floats)
+constexpr int kDenseRescan = 384;  // improved elements per warp above which lanes re-scan their own
 
 // Key scale M = 2*BS (a power of two, so scaling is exact) and the largest
 // finite panel sum a + b for which every key M*(a+b) + BS stays below 2^24.
@@ -182,6 +184,41 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
     }
   }
   if (!__any_sync(0xffffffffu, imp != 0)) return;
+  // Many improvements in this warp (early rounds): every lane re-runs its own
+  // candidates, 16 elements at a time, with k descending, so the last match
+  // it records is the first k whose sum equals the new value.
+  const int wcnt = __reduce_add_sync(0xffffffffu, __popcll(imp));
+  if (wcnt > kDenseRescan) {
+#pragma unroll
+    for (int a0 = 0; a0 < 8; a0 += 2) {
+      if (!__any_sync(0xffffffffu, ((imp >> (a0 * 8)) & 0xFFFF) != 0)) continue;
+      int pk[2][8];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) pk[q][c] = BS;
+      const int ra0 = mp_row(ty, a0), ra1 = mp_row(ty, a0 + 1);
+#pragma unroll 2
+      for (int k = BS - 1; k >= 0; --k) {
+        const float av[2] = {As[k * kSst + ra0], As[k * kSst + ra1]};
+        const float4 b0 = *reinterpret_cast<const float4*>(Bs + k * kSst + tx * 4);
+        const float4 b1 = *reinterpret_cast<const float4*>(Bs + k * kSst + 64 + tx * 4);
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (__fadd_rn(av[q], bv[c]) == d[a0 + q][c]) pk[q][c] = k;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if ((imp >> ((a0 + q) * 8 + c)) & 1)
+            P[(size_t)(r0 + mp_row(ty, a0 + q)) * ld + c0 + mp_col(tx, c)] = kb + pk[q][c];
+    }
+    return;
+  }
 #pragma unroll
   for (int slot = 0; slot < 64; ++slot) {
     unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);
