@@ -136,6 +136,17 @@ def _traffic_from_profile(n: int, bs: int):
         return None
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over all ranks (the slowest replica sets the job time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- CPU oracle legs
 
 def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: int, kind: str = "int"):
@@ -247,11 +258,7 @@ def run_gpu(args, rank: int, world: int):
         e1.record(s)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     flops = 2.0 * n ** 3
     value = flops * args.steps * world / (ms * 1e-3) / 1e9
 
@@ -318,6 +325,8 @@ def run_gpu(args, rank: int, world: int):
                        "ms_per_step": round(et * 1e3, 3), "steps": args.e2e_steps,
                        "api": "apsp_fw_host (pinned host buffers)"}
 
+    if args.autotune_c2:
+        line["n8192_autotuned"] = run_c2(args, dev)
     if args.batched:
         line["batched"] = run_batched(args, dev)
     if args.serve_seconds > 0:
@@ -354,6 +363,33 @@ def run_extra(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- batched and served workloads
+
+def run_c2(args, dev, n=8192, seed=2) -> dict:
+    """n=8192, integer weights U[1,1000], edge density 0.5; BS chosen by the library's autotuner."""
+    import torch
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+    bs, tune_ms = apsp.apsp_autotune_bs(n)
+    W = inputs.dense_digraph(n, seed, 1, 1000, density=0.5, device=dev)
+    D = torch.empty_like(W)
+    P = torch.empty((n, n), dtype=torch.int32, device=dev)
+    ws = torch.empty(apsp.apsp_fw_workspace_size(n, bs=bs, dtype=apsp.DTYPE_F32), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        apsp.apsp_fw_ex(W, D, P, bs=bs, dtype=apsp.DTYPE_F32, workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(3, args.steps)
+    e0.record()
+    for _ in range(steps):
+        apsp.apsp_fw_ex(W, D, P, bs=bs, dtype=apsp.DTYPE_F32, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "dense random digraph n=8192, integer weights U[1,1000], edge density 0.5",
+            "bs_autotuned": bs, "autotune_ms_bs32_64_128": [round(x, 3) for x in tune_ms],
+            "value": round(2.0 * n ** 3 / (ms * 1e-3) / 1e9, 1), "unit": "GFLOPS", "ms_per_step": round(ms, 3)}
+
 
 def run_batched(args, dev, count=4096, seed=6) -> dict:
     """4096 independent dense digraphs, n log-uniform in [16, 512], integer weights U[1,100],
@@ -500,6 +536,8 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=2560)
     ap.add_argument("--ref-sample-n", type=int, default=1536)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-c2", dest="autotune_c2", action="store_false",
+                    help="skip the n=8192 density-0.5 solve with the autotuned block size")
     ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serve"],
                     help="solve: the n=32768 single-graph line (with batched/served extras); "
                          "batched / serve: only that workload, as its own JSON line")

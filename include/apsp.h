@@ -99,6 +99,17 @@ typedef struct {
 /* Library default block size for order n (deterministic in n). */
 int apsp_default_bs(int n);
 
+/*
+ * Block-size autotuner. The paper tuned BS by hand for its machine (Section
+ * 5.2: 256 serial, 64 with 68 threads); this measures it on the current GPU:
+ * a synthetic dense integer-weight graph of order n is solved once per
+ * candidate BS in {32, 64, 128} after a warm-up, and *best_bs receives the
+ * fastest. ms_out (optional, 3 floats) receives the timed solve of each
+ * candidate. Allocates its graph with the stream-ordered allocator and
+ * synchronises `stream`. The choice is advisory: pass it as apsp_options.bs.
+ */
+apsp_status apsp_autotune_bs(int n, int* best_bs, float* ms_out, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* apsp_status_str(apsp_status s);
 

@@ -111,6 +111,9 @@ def load(build_if_missing: bool = True):
         L.apsp_batch_launch.restype = c_int
         L.apsp_batch_destroy.argtypes = [vp]
         L.apsp_batch_destroy.restype = c_int
+    if hasattr(L, "apsp_autotune_bs"):
+        L.apsp_autotune_bs.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float), vp]
+        L.apsp_autotune_bs.restype = c_int
     if hasattr(L, "apsp_fw_noalloc"):
         L.apsp_fw_noalloc.argtypes = [vp, vp, vp, c_int, ctypes.POINTER(apsp_options),
                                       ctypes.POINTER(apsp_run_info), vp]
@@ -169,6 +172,14 @@ def apsp_default_bs(n: int) -> int:
 
 def apsp_batched_bs(n: int) -> int:
     return int(load().apsp_batched_bs(int(n)))
+
+
+def apsp_autotune_bs(n: int, stream=None) -> tuple[int, list[float]]:
+    """apsp_autotune_bs: fastest BS in {32, 64, 128} for order n on this GPU, and the three timings (ms)."""
+    best = ctypes.c_int(0)
+    ms = (ctypes.c_float * 3)()
+    _check(load().apsp_autotune_bs(int(n), ctypes.byref(best), ms, _stream_ptr(stream)), "apsp_autotune_bs")
+    return int(best.value), [float(x) for x in ms]
 
 
 def apsp_fw_workspace_size(n: int, bs: int = 0, dtype: int = DTYPE_AUTO, validate: bool = True) -> int:

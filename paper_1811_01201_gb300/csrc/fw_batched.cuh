@@ -53,21 +53,29 @@ struct BatchQueue {
   unsigned int done;     // graphs finished
 };
 
-// Shared-memory layout (floats): diag[32][33], As[32][ldp], Bs[32][ldp]
+// Shared-memory layout (floats): diag[32][33], gR[32][36], gC[32][36], As[32][ldp], Bs[32][ldp]
+constexpr int kBG = 36;  // row stride of the key-form diagonal copies (16-byte aligned rows)
 __host__ __device__ constexpr int batched_ldp(int n_max) { return ((n_max + 31) / 32) * 32 + 8; }
 __host__ __device__ constexpr size_t batched_smem_bytes(int n_max) {
-  return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * batched_ldp(n_max)) + 64;
+  return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * kBG + 2 * (size_t)32 * batched_ldp(n_max)) + 64;
+}
+
+__device__ __forceinline__ float floor_small(float v) {
+  // floor for 0 <= v < 2^23 on the FMA pipe: round-down add of 2^23, then subtract
+  return __fsub_rn(__fadd_rd(v, 8388608.f), 8388608.f);
 }
 
 __device__ __forceinline__ float key_floor(float key) {
-  // M * floor(key / M): the value part of a key (exact for integer keys < 2^24)
-  return floorf(key * (1.f / kBKeyM)) * kBKeyM;
+  // M * floor(key / M): the value part of a key (exact for integer keys < 2^24; INF stays INF)
+  return floor_small(key * (1.f / kBKeyM)) * kBKeyM;
 }
 
 template <bool KEYED>
 __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, int ldp) {
   float* diag = sm;                 // [32][33]
-  float* As = sm + 32 * 33;         // As[k * ldp + i] = D[i][kb + k]   (column panel, transposed)
+  float* gR = sm + 32 * 33;         // gR[k * kBG + i] = M * diag[i][k] + k + 1   (key form, row-panel lines)
+  float* gC = gR + 32 * kBG;        // gC[k * kBG + j] = M * diag[k][j] + k + 1   (key form, column-panel lines)
+  float* As = gC + 32 * kBG;        // As[k * ldp + i] = D[i][kb + k]   (column panel, transposed)
   float* Bs = As + 32 * ldp;        // Bs[k * ldp + j] = D[kb + k][j]   (row panel)
   const int n = g.n;
   float* __restrict__ D = g.D;
@@ -119,7 +127,57 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
     }
 
     // ---------------- phase 2: lines of the row and column panels
-    {
+    if (KEYED) {
+      // key-form copies of the diagonal tile, then one thread per line with the
+      // line's 32 keys in registers: step k adds the line's own value part at k
+      for (int t = tid; t < 32 * 32; t += kBThreads) {
+        const int k = t >> 5, x = t & 31;
+        gR[k * kBG + x] = fmaf(diag[x * 33 + k], kBKeyM, (float)(k + 1));
+        gC[k * kBG + x] = fmaf(diag[k * 33 + x], kBKeyM, (float)(k + 1));
+      }
+      __syncthreads();
+      const int nl = n - kw;
+      for (int l = tid; l < 2 * nl; l += kBThreads) {
+        const bool rowp = l < nl;  // row-panel column o, else column-panel row o
+        int o = rowp ? l : l - nl;
+        o = o < kb ? o : o + kw;
+        const size_t base = rowp ? (size_t)kb * n + o : (size_t)o * n + kb;
+        const size_t stride = rowp ? (size_t)n : 1;
+        const float* g = rowp ? gR : gC;
+        float x[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) x[t] = t < kw ? D[base + t * stride] * kBKeyM : INF;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const float xk = key_floor(x[k]);
+#pragma unroll
+          for (int t = 0; t < 32; t += 4) {
+            const float4 g4 = *reinterpret_cast<const float4*>(g + k * kBG + t);
+            x[t] = fminf(x[t], __fadd_rn(g4.x, xk));
+            x[t + 1] = fminf(x[t + 1], __fadd_rn(g4.y, xk));
+            x[t + 2] = fminf(x[t + 2], __fadd_rn(g4.z, xk));
+            x[t + 3] = fminf(x[t + 3], __fadd_rn(g4.w, xk));
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          float v = INF;
+          if (t < kw) {
+            const float key = x[t];
+            if (key < INF) {
+              v = floor_small(key * (1.f / kBKeyM));
+              const int sl = (int)__fmaf_rn(-v, kBKeyM, key);
+              if (sl != 0) {
+                D[base + t * stride] = v;
+                P[base + t * stride] = kb + sl - 1;
+              }
+            }
+          }
+          if (rowp) Bs[t * ldp + o] = v * kBKeyM;
+          else As[t * ldp + o] = fmaf(v, kBKeyM, (float)(t + 1));
+        }
+      }
+    } else {
       // lane t: row t of the diagonal tile (row-panel lines) and column t (column-panel lines)
       float drow[32], dcol[32];
 #pragma unroll
@@ -141,7 +199,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        Bs[lane * ldp + o] = valid ? (KEYED ? x * kBKeyM : x) : INF;
+        Bs[lane * ldp + o] = valid ? x : INF;
       }
       // column-panel row o: element t = D[o][kb+t]; c_t = x_k + Diag[k][t]
       for (int l = warp; l < nl; l += NW) {
@@ -155,7 +213,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        As[lane * ldp + o] = valid ? (KEYED ? fmaf(x, kBKeyM, (float)(lane + 1)) : x) : INF;
+        As[lane * ldp + o] = valid ? x : INF;
       }
     }
     __syncthreads();
@@ -213,8 +271,8 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
               const float key = d[a][c];
               if (i >= n || j >= n || !(key < INF)) continue;
               if ((i >= kb && i < kb + kw) || (j >= kb && j < kb + kw)) continue;
-              const float v = floorf(key * (1.f / kBKeyM));
-              const int sl = (int)(key - v * kBKeyM);
+              const float v = floor_small(key * (1.f / kBKeyM));
+              const int sl = (int)__fmaf_rn(-v, kBKeyM, key);
               if (sl != 0) {
                 D[(size_t)i * n + j] = v;
                 P[(size_t)i * n + j] = kb + sl - 1;

@@ -29,17 +29,17 @@
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads, 8 x 8 elements per
 // thread in registers (rows ty*4+{0..3}, 64+ty*4+{0..3}; columns likewise
-// with tx). The A panel slice (128 x BS) is stored transposed and the B panel
-// slice (BS x 128) as is, both with a padded row stride of 132 floats, so the
-// per-k fragment loads are 128-bit and conflict-free. Rows/columns of the
-// tile that fall in block r (the panels) are computed but never written.
+// with tx). Both panel slices are stored as k pairs (A transposed), so each
+// 128-bit shared load gives two elements' (a_k, a_k+1) pairs and one PTX
+// add.rn.f32x2 forms two candidates; the min stays one FMNMX per candidate.
+// Rows/columns of the tile that fall in block r (the panels) are computed but
+// never written.
 #pragma once
 
 #include "fw_common.cuh"
 
 namespace apsp {
 
-constexpr int kSst = kTile + 4;  // shared row stride (floats)
 constexpr int kDenseRescan = 384;  // improved elements per warp above which lanes re-scan their own
 
 // Key scale M = 2*BS (a power of two, so scaling is exact) and the largest
@@ -51,10 +51,29 @@ struct KeyParams {
   static_assert(BS == 32 || BS == 64 || BS == 128, "unsupported block size");
 };
 
+// Panels are stored as k pairs: As[kp*kS2 + 2i + e] = A[i][2kp+e] and
+// Bs[kp*kS2 + 2j + e] = B[2kp+e][j], so one 128-bit load gives two rows' (or
+// columns') consecutive-k pairs and one add.rn.f32x2 forms two candidates.
+constexpr int kS2 = 2 * kTile + 8;  // floats per k-pair row (padded)
+
 template <int BS>
 constexpr size_t minplus_f32_smem_bytes() {
-  return sizeof(float) * 2 * (size_t)BS * kSst;
+  return sizeof(float) * (size_t)BS * kS2;
 }
+
+__device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
+  // two independent IEEE round-to-nearest fp32 additions in one instruction
+  unsigned long long pa, pb, pc;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(pa) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(pb) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(pc) : "l"(pa), "l"(pb));
+  float2 c;
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(pc));
+  return c;
+}
+
+__device__ __forceinline__ float pan(const float* S, int k, int x) { return S[(k >> 1) * kS2 + 2 * x + (k & 1)]; }
+
 
 __device__ __forceinline__ int mp_row(int ty, int a) { return (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
 __device__ __forceinline__ int mp_col(int tx, int c) { return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
@@ -83,13 +102,17 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
     d[a][4] = v1.x; d[a][5] = v1.y; d[a][6] = v1.z; d[a][7] = v1.w;
   }
   const float mb = keyed ? M : 1.f;
+  // B panel slice: rows 2kp and 2kp+1 of one column quad -> two interleaved 128-bit stores
 #pragma unroll
-  for (int m = 0; m < BS / 8; ++m) {
-    const int idx = tid + 256 * m, k = idx >> 5, q = idx & 31;
-    float4 v = *reinterpret_cast<const float4*>(D + (size_t)(kb + k) * ld + c0 + q * 4);
-    v.x *= mb; v.y *= mb; v.z *= mb; v.w *= mb;
-    *reinterpret_cast<float4*>(Bs + k * kSst + q * 4) = v;
+  for (int m = 0; m < BS / 16; ++m) {
+    const int idx = tid + 256 * m, kp = idx >> 5, q = idx & 31;
+    const float4 x = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp) * ld + c0 + q * 4);
+    const float4 y = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp + 1) * ld + c0 + q * 4);
+    *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
+    *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
   }
+  // A panel slice: 128 rows x BS columns; a 128-bit load of row i holds k = 4q4..4q4+3, i.e. two
+  // k pairs. Lane -> (row ri = lane & 7 of an 8-row group, column quad cq = lane >> 3).
 #pragma unroll
   for (int m = 0; m < BS / 8; ++m) {
     const int idx = tid + 256 * m;
@@ -97,11 +120,10 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
     const int i = (grp % (kTile / 8)) * 8 + ri;
     const int q4 = (grp / (kTile / 8)) * 4 + cq;
     const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
-    const float add0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
-    As[(q4 * 4 + 0) * kSst + i] = fmaf(v.x, mb, add0);
-    As[(q4 * 4 + 1) * kSst + i] = fmaf(v.y, mb, keyed ? add0 + 1.f : 0.f);
-    As[(q4 * 4 + 2) * kSst + i] = fmaf(v.z, mb, keyed ? add0 + 2.f : 0.f);
-    As[(q4 * 4 + 3) * kSst + i] = fmaf(v.w, mb, keyed ? add0 + 3.f : 0.f);
+    const float k0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
+    const float k1 = keyed ? k0 + 1.f : 0.f, k2 = keyed ? k0 + 2.f : 0.f, k3 = keyed ? k0 + 3.f : 0.f;
+    *reinterpret_cast<float2*>(As + (2 * q4) * kS2 + 2 * i) = make_float2(fmaf(v.x, mb, k0), fmaf(v.y, mb, k1));
+    *reinterpret_cast<float2*>(As + (2 * q4 + 1) * kS2 + 2 * i) = make_float2(fmaf(v.z, mb, k2), fmaf(v.w, mb, k3));
   }
   if (keyed) {
 #pragma unroll
@@ -110,20 +132,30 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
       for (int c = 0; c < 8; ++c) d[a][c] *= M;
   }
   __syncthreads();
-  const float* Ap = As + ty * 4;
-  const float* Bp = Bs + tx * 4;
-#pragma unroll 4
-  for (int k = 0; k < BS; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * kSst);
-    const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * kSst + 64);
-    const float4 b0 = *reinterpret_cast<const float4*>(Bp + k * kSst);
-    const float4 b1 = *reinterpret_cast<const float4*>(Bp + k * kSst + 64);
-    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  // Hot loop: per k pair, one f32x2 add and two FMNMX per element.
+  const float* Ap = As + ty * 8;
+  const float* Bp = Bs + tx * 8;
+#pragma unroll 2
+  for (int kp = 0; kp < BS / 2; ++kp) {
+    const float4 a0 = *reinterpret_cast<const float4*>(Ap + kp * kS2);
+    const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
+    const float4 a2 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 128);
+    const float4 a3 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 132);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bp + kp * kS2);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 4);
+    const float4 b2 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 128);
+    const float4 b3 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 132);
+    const float2 av[8] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}, {a1.z, a1.w},
+                          {a2.x, a2.y}, {a2.z, a2.w}, {a3.x, a3.y}, {a3.z, a3.w}};
+    const float2 bv[8] = {{b0.x, b0.y}, {b0.z, b0.w}, {b1.x, b1.y}, {b1.z, b1.w},
+                          {b2.x, b2.y}, {b2.z, b2.w}, {b3.x, b3.y}, {b3.z, b3.w}};
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
+      for (int c = 0; c < 8; ++c) {
+        const float2 s = fadd2_rn(av[a], bv[c]);
+        d[a][c] = fminf(fminf(d[a][c], s.x), s.y);
+      }
   }
   if (keyed) {
 #pragma unroll
@@ -200,10 +232,10 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
       const int ra0 = mp_row(ty, a0), ra1 = mp_row(ty, a0 + 1);
 #pragma unroll 2
       for (int k = BS - 1; k >= 0; --k) {
-        const float av[2] = {As[k * kSst + ra0], As[k * kSst + ra1]};
-        const float4 b0 = *reinterpret_cast<const float4*>(Bs + k * kSst + tx * 4);
-        const float4 b1 = *reinterpret_cast<const float4*>(Bs + k * kSst + 64 + tx * 4);
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float av[2] = {pan(As, k, ra0), pan(As, k, ra1)};
+        float bv[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) bv[c] = pan(Bs, k, mp_col(tx, c));
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -235,7 +267,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
 #pragma unroll
       for (int m = 0; m < BS / 32; ++m) {
         const int k = m * 32 + lane;
-        const float cand = __fadd_rn(As[k * kSst + li], Bs[k * kSst + lj]);
+        const float cand = __fadd_rn(pan(As, k, li), pan(Bs, k, lj));
         const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
         if (eq && kstar == BS) kstar = m * 32 + __ffs(eq) - 1;
       }
@@ -269,7 +301,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
   const bool keyed = graph_int != 0 &&
                      __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
   if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
-  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, sm, sm + BS * kSst);
+  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, sm, sm + (BS / 2) * kS2);
 }
 
 }  // namespace apsp

@@ -291,3 +291,14 @@ def test_full_n32768_real():
 @pytest.mark.slow
 def test_full_n32768_u16():
     _sampled_check(32768, 5, 1, 2, 1.0, "int", bs=64, n_src=4, expect_dtype=apsp.DTYPE_U16X2)
+
+
+def test_autotuner_returns_a_valid_block_size():
+    bs, ms = apsp.apsp_autotune_bs(1024)
+    assert bs in (32, 64, 128)
+    assert all(t > 0 for t in ms)
+    assert ms[(32, 64, 128).index(bs)] == min(ms)
+    W = inputs.dense_digraph(1024, seed=77, lo=1, hi=100, density=0.5)
+    D, P, info = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    assert info.bs_used == bs
+    _expect_exact(W, D, P, bs)
