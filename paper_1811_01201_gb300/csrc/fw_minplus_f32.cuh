@@ -135,7 +135,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
   // Hot loop: per k pair, one f32x2 add and two FMNMX per element.
   const float* Ap = As + ty * 8;
   const float* Bp = Bs + tx * 8;
-#pragma unroll 2
+#pragma unroll 1
   for (int kp = 0; kp < BS / 2; ++kp) {
     const float4 a0 = *reinterpret_cast<const float4*>(Ap + kp * kS2);
     const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
