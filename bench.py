@@ -531,7 +531,7 @@ def main():
                     help="weights: integer U[1,1000] (default) or real U(0,1]")
     ap.add_argument("--no-u16", dest="u16", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample-n", type=int, default=2560)
     ap.add_argument("--ref-sample-n", type=int, default=1536)

@@ -335,21 +335,24 @@ extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n
   ServerImpl& s = srv->impl;
   const size_t nn = (size_t)n * n;
   // host-side validation and 16-bit eligibility (same rule as apsp_fw)
-  bool frac = false;
+  bool frac = false, bad = false;
   float mx = 0.f;
-  for (size_t t = 0; t < nn; ++t) {
-    const size_t i = t / n, j = t - i * n;
-    if (i == j) continue;
-    const float v = W[t];
-    if (!(v >= 0.f)) {  // negative or NaN
-      std::lock_guard<std::mutex> g(s.m);
-      ++s.rejected;
-      return APSP_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const float* row = W + (size_t)i * n;
+    for (int j = 0; j < n; ++j) {
+      const float v = row[j];
+      if (j == i) continue;
+      bad |= !(v >= 0.f);  // negative or NaN
+      if (v < INFINITY) {
+        frac |= v != std::floor(v);
+        mx = v > mx ? v : mx;
+      }
     }
-    if (std::isfinite(v)) {
-      if (v != std::floor(v)) frac = true;
-      mx = std::max(mx, v);
-    }
+  }
+  if (bad) {
+    std::lock_guard<std::mutex> g(s.m);
+    ++s.rejected;
+    return APSP_EINVAL;
   }
   auto j = std::make_shared<Job>();
   j->n = n;

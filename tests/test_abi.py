@@ -81,3 +81,23 @@ def test_argument_checks_return_status_without_touching_the_gpu():
     assert L.apsp_serve_stats(None, None) == apsp.APSP_EINVAL
     assert L.apsp_serve_destroy(None) == apsp.APSP_EINVAL
     assert L.apsp_batched_bs(100) == 32
+
+
+def test_size_limits_rejected_on_the_host():
+    # non-null placeholder pointers: the checks on n and options come before any CUDA call
+    L = apsp.load()
+    fake = ctypes.c_void_p(256)
+    o = apsp.apsp_options(0, apsp.DTYPE_F32, 0, 0)
+    assert L.apsp_fw_ex(fake, fake, fake, 65537, ctypes.byref(o), None, 0, None, None) == apsp.APSP_EINVAL
+    assert L.apsp_fw_ex(fake, fake, fake, -5, ctypes.byref(o), None, 0, None, None) == apsp.APSP_EINVAL
+    o_bad = apsp.apsp_options(0, 7, 1, 0)  # unknown dtype
+    assert L.apsp_fw_ex(fake, fake, fake, 64, ctypes.byref(o_bad), None, 0, None, None) == apsp.APSP_EINVAL
+    o_u16 = apsp.apsp_options(0, apsp.DTYPE_U16X2, 0, 0)  # 16-bit needs the validation scan
+    assert L.apsp_fw_ex(fake, fake, fake, 64, ctypes.byref(o_u16), None, 0, None, None) == apsp.APSP_EINVAL
+    # misaligned caller workspace
+    assert L.apsp_fw_ex(fake, fake, fake, 64, ctypes.byref(o), ctypes.c_void_p(4096 + 8), 1 << 20, None,
+                        None) == apsp.APSP_EINVAL
+    n_arr = (ctypes.c_int * 1)(513)
+    ptrs = (ctypes.c_void_p * 1)(256)
+    out = ctypes.c_void_p()
+    assert L.apsp_batch_create(ptrs, ptrs, ptrs, n_arr, 1, None, ctypes.byref(out), None) == apsp.APSP_EINVAL

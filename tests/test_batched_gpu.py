@@ -119,3 +119,29 @@ def test_invalid_batches_rejected():
     Ws, Wd, Dd, Pd = _make([45], 14)
     apsp.apsp_fw_batched(Wd, Dd, Pd)
     _check_all(Ws, Dd, Pd)
+
+
+def test_full_size_batch_in_cuda_graph_sampled():
+    # the benchmark's batch (4096 graphs, n log-uniform in [16,512], U[1,100], density 0.7) run as
+    # one CUDA-graph-replayed persistent launch; 48 sampled graphs checked against the oracle
+    count, seed = 4096, 6
+    ns = inputs.batch_sizes(count, seed)
+    Wd = [inputs.dense_digraph(n, inputs.batch_graph_seed(seed, g), 1, 100, density=0.7, device=DEV)
+          for g, n in enumerate(ns)]
+    Dd = [torch.empty_like(w) for w in Wd]
+    Pd = [torch.empty(w.shape, dtype=torch.int32, device=DEV) for w in Wd]
+    b = apsp.Batch(Wd, Dd, Pd)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.launch(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    sample = list(rng.choice(count, size=44, replace=False)) + [int(np.argmax(ns)), int(np.argmin(ns))]
+    for g in sample:
+        Dr, Pr = oracle.fw_blocked(Wd[g].cpu().numpy(), 32)
+        np.testing.assert_array_equal(Dd[g].cpu().numpy(), Dr)
+        np.testing.assert_array_equal(Pd[g].cpu().numpy(), Pr)
+    b.close()
