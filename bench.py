@@ -304,6 +304,10 @@ def run_gpu(args, rank: int, world: int):
                          "peak_tflops": round(ALU_PEAK_U16_TFLOPS, 2)}
         del Wu, wsu
 
+    # Path reconstruction on the device from the solve's P (apsp_paths), seeded random pairs.
+    if args.paths > 0:
+        line["paths"] = run_paths(args, dev, P, n, args.paths)
+
     # End to end through apsp_fw_host: host pinned W in, host D and P out, every step.
     if args.e2e:
         Wh = W.cpu().pin_memory()
@@ -336,6 +340,39 @@ def run_gpu(args, rank: int, world: int):
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_paths(args, dev, P, n: int, count: int, cap: int = 64, reps: int = 5) -> dict:
+    """apsp_paths over `count` seeded random (i, j) pairs of the solved n-vertex graph: one thread
+    walks one pair; a path of L vertices costs 2L - 3 dependent random reads of P."""
+    import torch
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+    pairs = inputs.vertex_pairs(count, n, 11, device=dev)
+    out = torch.empty((count, cap), dtype=torch.int32, device=dev)
+    lens = torch.empty((count,), dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        apsp.apsp_paths(P, pairs, cap, out, lens)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        apsp.apsp_paths(P, pairs, cap, out, lens)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    L = lens.to(torch.int64)
+    ok = L >= 2
+    reads = int((2 * L[ok] - 3).sum())
+    return {"workload": f"{count} random (i, j) pairs of the solved graph, cap {cap}",
+            "paths_per_s": round(count / (ms * 1e-3), 1), "ms": round(ms, 4),
+            "mean_vertices": round(float(L[ok].float().mean()), 3), "failed": int((L < 0).sum()),
+            "same_vertex_pairs": int((L == 1).sum()),
+            "p_reads_per_s": round(reads / (ms * 1e-3), 1),
+            "sector_gbs": round(32.0 * reads / (ms * 1e-3) / 1e9, 1), "launches_per_call": 1}
 
 
 def run_extra(args, rank: int, world: int):
@@ -531,6 +568,7 @@ def main():
                     help="weights: integer U[1,1000] (default) or real U(0,1]")
     ap.add_argument("--no-u16", dest="u16", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--paths", type=int, default=1 << 20, help="pairs for the apsp_paths line (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample-n", type=int, default=2560)

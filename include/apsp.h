@@ -276,6 +276,31 @@ apsp_status apsp_fw_noalloc(const float* W, float* D, int32_t* P, int n, const a
 /* Size of the fixed array apsp_fw_noalloc works in (APSP_NOALLOC_SCRATCH_BYTES). */
 size_t apsp_noalloc_scratch_bytes(void);
 
+/* ---------------------------------------------------------------- path reconstruction */
+
+/*
+ * Section 3 of arXiv 1811.01201: P[i][j] is the intermediate vertex added last
+ * to the path i -> j, kept for rebuilding the path; the path is
+ * path(i, P[i][j]) followed by path(P[i][j], j), and P == -1 is the direct
+ * edge.
+ *
+ * apsp_paths: batched walks of a DEVICE P, one thread per pair.
+ *   P:     device, n*n int32, row-major, leading dimension n (as apsp_fw* write it).
+ *   pairs: device, 2*count int32: the (i, j) pairs, i first.
+ *   out:   device, count*cap int32: path t is out[t*cap .. t*cap + len[t] - 1]
+ *          (i first, j last); the rest of the row is overwritten as scratch.
+ *   len:   device, count int32: the vertex count of each path, or -1 exactly
+ *          where apsp_path (below) returns -1 for the same P, pair and cap.
+ * Vertex lists equal apsp_path's on a host copy of P. The buffers stay the
+ * caller's. Asynchronous on `stream` (one kernel launch, no allocation, so it
+ * may be captured into a CUDA graph).
+ * Errors: APSP_EINVAL for n < 1, count < 0, cap < 1 or a null pointer with
+ * count > 0 (nothing launched); APSP_ECUDA if the launch fails. count == 0
+ * launches nothing.
+ */
+apsp_status apsp_paths(const int32_t* P, int n, const int32_t* pairs, int count, int32_t* out, int cap,
+                       int32_t* len, void* stream);
+
 /* ---------------------------------------------------------------- host helpers */
 
 /*

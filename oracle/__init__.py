@@ -146,12 +146,14 @@ def bellman_ford(W: np.ndarray, src: int) -> np.ndarray:
     return out
 
 
-def path(P: np.ndarray, i: int, j: int):
-    """Vertices of the path i -> j encoded in P, or None if the walk is malformed."""
+def path(P: np.ndarray, i: int, j: int, cap: int | None = None):
+    """Vertices of the path i -> j encoded in P (at most cap, default n), or None if the walk
+    is malformed or longer."""
     P = np.ascontiguousarray(P, dtype=np.int32)
     n = _square(P)
-    out = np.empty(max(n, 1), dtype=np.int32)
-    cnt = _load().oracle_path(_ptr(P, ctypes.c_int32), n, int(i), int(j), _ptr(out, ctypes.c_int32), n)
+    cap = n if cap is None else int(cap)
+    out = np.empty(max(cap, 1), dtype=np.int32)
+    cnt = _load().oracle_path(_ptr(P, ctypes.c_int32), n, int(i), int(j), _ptr(out, ctypes.c_int32), cap)
     return None if cnt < 0 else [int(v) for v in out[:cnt]]
 
 

@@ -96,6 +96,8 @@ def load(build_if_missing: bool = True):
     L.apsp_fw_host.restype = c_int
     L.apsp_path.argtypes = [i32p, c_int, c_int, c_int, i32p, c_int]
     L.apsp_path.restype = c_int
+    L.apsp_paths.argtypes = [vp, c_int, vp, c_int, vp, c_int, vp, vp]
+    L.apsp_paths.restype = c_int
     if hasattr(L, "apsp_fw_batched"):
         L.apsp_fw_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(c_int), c_int, ctypes.POINTER(apsp_options),
@@ -308,16 +310,41 @@ class Batch:
             pass
 
 
-def apsp_path(P: np.ndarray | torch.Tensor, i: int, j: int) -> list[int] | None:
-    """apsp_path on a host copy of P: vertex list i..j, or None if malformed."""
+def apsp_path(P: np.ndarray | torch.Tensor, i: int, j: int, cap: int | None = None) -> list[int] | None:
+    """apsp_path on a host copy of P: vertex list i..j (at most cap, default n), or None if malformed."""
     if isinstance(P, torch.Tensor):
         P = P.cpu().numpy()
     P = np.ascontiguousarray(P, dtype=np.int32)
     n = int(P.shape[0])
-    out = np.empty(max(n, 1), dtype=np.int32)
+    cap = n if cap is None else int(cap)
+    out = np.empty(max(cap, 1), dtype=np.int32)
     i32p = ctypes.POINTER(ctypes.c_int32)
-    cnt = load().apsp_path(P.ctypes.data_as(i32p), n, int(i), int(j), out.ctypes.data_as(i32p), n)
+    cnt = load().apsp_path(P.ctypes.data_as(i32p), n, int(i), int(j), out.ctypes.data_as(i32p), cap)
     return None if cnt < 0 else [int(v) for v in out[:cnt]]
+
+
+def apsp_paths(P: torch.Tensor, pairs: torch.Tensor, cap: int = 64, out: torch.Tensor | None = None,
+               lens: torch.Tensor | None = None, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """apsp_paths: walk a device P for every (i, j) row of `pairs` (int32, shape (count, 2)) on the
+    GPU. Returns (out, lens): out[t, :lens[t]] are the vertices of path t, lens[t] == -1 where the
+    walk fails (as apsp_path). Asynchronous on `stream`."""
+    n = int(P.shape[0])
+    _dev_ptr(P, torch.int32, n, "P")
+    if not isinstance(pairs, torch.Tensor) or not pairs.is_cuda or pairs.dtype != torch.int32 \
+            or not pairs.is_contiguous() or pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be a contiguous CUDA int32 tensor of shape (count, 2)")
+    count = int(pairs.shape[0])
+    if out is None:
+        out = torch.empty((count, cap), dtype=torch.int32, device=P.device)
+    if lens is None:
+        lens = torch.empty((count,), dtype=torch.int32, device=P.device)
+    if not out.is_cuda or out.dtype != torch.int32 or not out.is_contiguous() or out.numel() != count * cap:
+        raise ValueError("out must be a contiguous CUDA int32 tensor with count*cap elements")
+    if not lens.is_cuda or lens.dtype != torch.int32 or not lens.is_contiguous() or lens.numel() != count:
+        raise ValueError("lens must be a contiguous CUDA int32 tensor with count elements")
+    _check(load().apsp_paths(P.data_ptr(), n, pairs.data_ptr(), count, out.data_ptr(), int(cap), lens.data_ptr(),
+                             _stream_ptr(stream)), "apsp_paths")
+    return out, lens
 
 
 class Server:

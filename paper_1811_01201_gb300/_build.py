@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libapsp.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["apsp_fw.cu", "apsp_batched.cu", "apsp_serve.cu", "apsp_noalloc.cu", "apsp_tune.cu", "apsp_host.cpp"]
+SOURCES = ["apsp_fw.cu", "apsp_batched.cu", "apsp_serve.cu", "apsp_noalloc.cu", "apsp_tune.cu", "apsp_paths.cu",
+           "apsp_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-I" + os.path.join(ROOT, "include")]

@@ -90,16 +90,19 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   const size_t ld = (size_t)n_pad;
   constexpr size_t sm2 = phase2_smem_bytes<T, BS>();
   constexpr size_t sm3 = std::is_same<T, F32T>::value ? minplus_f32_smem_bytes<BS>() : minplus_u16_smem_bytes<BS>();
+  constexpr size_t sm3r = minplus_f32_smem_bytes<BS, true>();
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
     cudaError_t e1 = cudaFuncSetAttribute(fw_phase2_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-    cudaError_t e2;
-    if constexpr (std::is_same<T, F32T>::value)
-      e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-    else
+    cudaError_t e2, e3 = cudaSuccess;
+    if constexpr (std::is_same<T, F32T>::value) {
+      e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+      e3 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3r);
+    } else {
       e2 = cudaFuncSetAttribute(fw_phase3_u16_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-    attr_err = e1 != cudaSuccess ? e1 : e2;
+    }
+    attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int sms = sm_count();
@@ -110,9 +113,12 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
     if (R > 1) {
       fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm);
       tm.mark(1);
-      if constexpr (std::is_same<T, F32T>::value)
-        fw_phase3_f32_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, kStaggerCycles, sms);
-      else
+      if constexpr (std::is_same<T, F32T>::value) {
+        if (graph_int)
+          fw_phase3_f32_kernel<BS, false><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, kStaggerCycles, sms);
+        else
+          fw_phase3_f32_kernel<BS, true><<<nT * nT, 256, sm3r, s>>>(D, P, ld, nT, r, rm, 0, kStaggerCycles, sms);
+      } else
         fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, kStaggerCycles, sms);
       tm.mark(2);
     }

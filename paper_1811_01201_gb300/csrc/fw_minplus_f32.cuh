@@ -21,11 +21,13 @@
 //    ties, as the strict '<' requires. Slot 0 in the result means unchanged,
 //    so neither the old tile nor a search is needed: P comes for free.
 //  * otherwise (real-valued weights, large distances): improved elements are
-//    found by comparing with the old D. Where few improved, each warp
-//    re-evaluates the BS candidates of one improved element at a time, one k
-//    per lane, taking the first lane whose sum equals D'; where many improved
-//    (early rounds), every lane re-scans its own elements with k descending.
-//    Both use the bit-identical FADD, so equality is exact.
+//    found by comparing with the old D. On real-valued graphs the warp lists
+//    the improved elements in shared memory and each lane scans one listed
+//    element's candidates with k ascending up to the first whose sum equals
+//    D'. On integer graphs (whose rounds without keys are rare), where many
+//    improved every lane re-scans its own elements with k descending, else
+//    the warp re-evaluates one improved element at a time, one k per lane.
+//    All use bit-identical additions, so equality is exact.
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads, 8 x 8 elements per
 // thread in registers (rows ty*4+{0..3}, 64+ty*4+{0..3}; columns likewise
@@ -56,9 +58,13 @@ struct KeyParams {
 // columns') consecutive-k pairs and one add.rn.f32x2 forms two candidates.
 constexpr int kS2 = 2 * kTile + 8;  // floats per k-pair row (padded)
 
-template <int BS>
+// Per-warp list of improved elements for the P search of real-valued graphs.
+constexpr int kQueuePerWarp = 384;
+constexpr int kQueueFlush = kQueuePerWarp - 256;
+
+template <int BS, bool REAL = false>
 constexpr size_t minplus_f32_smem_bytes() {
-  return sizeof(float) * (size_t)BS * kS2;
+  return sizeof(float) * (size_t)BS * kS2 + (REAL ? sizeof(int2) * 8 * kQueuePerWarp : 0);
 }
 
 __device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
@@ -85,9 +91,14 @@ __device__ __forceinline__ float floor_pos(float v) {
   return __fsub_rn(__fadd_rd(v, 8388608.f), 8388608.f);
 }
 
-template <int BS>
+// REAL: the graph has non-integer weights, so keys never apply and every
+// improved element goes through a per-warp list. Integer graphs keep the short
+// search code (their rounds without keys are rare), which leaves the key
+// path's registers alone.
+template <int BS, bool REAL>
 __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __restrict__ P, size_t ld, int kb,
-                                          int r0, int c0, bool keyed, float* As, float* Bs) {
+                                          int r0, int c0, bool keyed_in, float* As, float* Bs, int2* queue) {
+  const bool keyed = REAL ? false : keyed_in;
   constexpr float M = KeyParams<BS>::M;
   const float INF = f32_inf();
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -185,6 +196,73 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
           for (int e = 0; e < 4; ++e)
             if (sl[e] != 0) P[(size_t)gi * ld + gj + e] = kb + sl[e] - 1;
         }
+      }
+    }
+    return;
+  }
+  if constexpr (REAL) {
+    // Row by row: compare with the old D, write the improved values, and list
+    // the improved elements (row << 8 | column, new value) in the warp's
+    // shared-memory queue. Once the queue holds kQueueFlush or more (a row adds
+    // at most 256), each lane takes listed elements and scans their candidates
+    // with k ascending up to the first whose sum equals the new value.
+    int2* wq = queue + warp * kQueuePerWarp;
+    const unsigned lt = (1u << lane) - 1u;
+    int cnt = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int li = mp_row(ty, a);
+      const int gi = r0 + li;
+      const bool band_r = (gi >= kb) && (gi < kb + BS);
+      unsigned rimp = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gj = c0 + mp_col(tx, 4 * h);
+        const bool band_c = (gj >= kb) && (gj < kb + BS);
+        if (band_r || band_c) continue;
+        float* dp = D + (size_t)gi * ld + gj;
+        const float4 o4 = *reinterpret_cast<const float4*>(dp);
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        float nv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool im = d[a][4 * h + e] < old[e];
+          nv[e] = im ? d[a][4 * h + e] : old[e];
+          if (im) rimp |= 1u << (4 * h + e);
+        }
+        if (rimp >> (4 * h)) *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const bool bit = (rimp >> c) & 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        if (bit) wq[cnt + __popc(bal & lt)] = make_int2((li << 8) | mp_col(tx, c), __float_as_int(d[a][c]));
+        cnt += __popc(bal);
+      }
+      if (cnt >= kQueueFlush || (a == 7 && cnt > 0)) {
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32) {
+          const int2 ent = wq[e];
+          const int qi = ent.x >> 8, qj = ent.x & 255;
+          const float dn = __int_as_float(ent.y);
+          int kstar = BS;
+#pragma unroll 1
+          for (int kp = 0; kp < BS / 2; ++kp) {
+            const float2 c2 = fadd2_rn(*reinterpret_cast<const float2*>(As + kp * kS2 + 2 * qi),
+                                       *reinterpret_cast<const float2*>(Bs + kp * kS2 + 2 * qj));
+            if (c2.x == dn) {
+              kstar = 2 * kp;
+              break;
+            }
+            if (c2.y == dn) {
+              kstar = 2 * kp + 1;
+              break;
+            }
+          }
+          P[(size_t)(r0 + qi) * ld + c0 + qj] = kb + kstar;
+        }
+        __syncwarp();
+        cnt = 0;
       }
     }
     return;
@@ -288,7 +366,7 @@ __device__ __forceinline__ void spin_cycles(long long cycles) {
 //   stagger:   CTAs sms .. 2*sms-1 (the first wave's second half) start this
 //              many cycles late, so the first wave's SMs do not all load their
 //              tiles from HBM at the same instant
-template <int BS>
+template <int BS, bool REAL>
 __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
                                                                size_t ld, int nT, int r, const RoundMax* __restrict__ rm,
                                                                int graph_int, int stagger, int sms) {
@@ -298,10 +376,10 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
   const int r0 = tr * kTile, c0 = tc * kTile;
   // Tiles entirely inside row band r or column band r belong to phases 1-2.
   if ((r0 >= kb && r0 + kTile <= kb + BS) || (c0 >= kb && c0 + kTile <= kb + BS)) return;
-  const bool keyed = graph_int != 0 &&
+  const bool keyed = !REAL && graph_int != 0 &&
                      __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
   if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
-  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, sm, sm + (BS / 2) * kS2);
+  tile_body<BS, REAL>(D, P, ld, kb, r0, c0, keyed, sm, sm + (BS / 2) * kS2, reinterpret_cast<int2*>(sm + BS * kS2));
 }
 
 }  // namespace apsp

@@ -64,6 +64,13 @@ def uniform24(seed: int, stream: int, idx: torch.Tensor) -> torch.Tensor:
 
 STREAM_WEIGHT = 0
 STREAM_EDGE = 1
+STREAM_PAIR = 2
+
+
+def vertex_pairs(count: int, n: int, seed: int, device="cpu") -> torch.Tensor:
+    """``count`` seeded (i, j) vertex pairs, uniform over [0, n)^2, as a (count, 2) int32 tensor."""
+    u = uniform24(seed, STREAM_PAIR, torch.arange(2 * count, dtype=torch.int64, device=device))
+    return ((u * n) >> 24).to(torch.int32).view(count, 2).contiguous()
 
 
 def dense_digraph(n: int, seed: int, lo: float = 1, hi: float = 100, density: float = 1.0, kind: str = "int",

@@ -62,6 +62,28 @@ def test_path_helper_matches_oracle_walk():
     bad = P.copy()
     bad[0, 1] = 0  # intermediate equal to an endpoint
     assert apsp.apsp_path(bad, 0, 1) is None
+    # a capacity below the path's vertex count fails; exactly the count succeeds
+    for i, j in [(0, 69), (5, 33), (60, 2)]:
+        full = oracle.path(P, i, j)
+        assert apsp.apsp_path(P, i, j, cap=len(full)) == full
+        assert apsp.apsp_path(P, i, j, cap=len(full) - 1) is None
+        assert oracle.path(P, i, j, cap=len(full) - 1) is None
+
+
+def test_path_helper_matches_oracle_on_malformed_matrices():
+    import oracle
+    # random P over [-1, n): cycles, self-references and long walks; host helper and oracle
+    # agree on every pair and capacity (both the vertex list and the failure)
+    rng = np.random.default_rng(4)
+    for trial in range(30):
+        n = int(rng.integers(2, 12))
+        P = rng.integers(-1, n, size=(n, n)).astype(np.int32)
+        if trial % 3 == 0:
+            P[rng.random((n, n)) < 0.6] = -1
+        for cap in (1, 2, 3, 5, n, 2 * n):
+            for i in range(n):
+                for j in range(n):
+                    assert apsp.apsp_path(P, i, j, cap) == oracle.path(P, i, j, cap), (trial, cap, i, j)
 
 
 def test_argument_checks_return_status_without_touching_the_gpu():
@@ -81,6 +103,12 @@ def test_argument_checks_return_status_without_touching_the_gpu():
     assert L.apsp_serve_stats(None, None) == apsp.APSP_EINVAL
     assert L.apsp_serve_destroy(None) == apsp.APSP_EINVAL
     assert L.apsp_batched_bs(100) == 32
+    fake = ctypes.c_void_p(256)
+    assert L.apsp_paths(fake, 0, fake, 4, fake, 8, fake, None) == apsp.APSP_EINVAL     # n < 1
+    assert L.apsp_paths(fake, 16, fake, -1, fake, 8, fake, None) == apsp.APSP_EINVAL   # count < 0
+    assert L.apsp_paths(fake, 16, fake, 4, fake, 0, fake, None) == apsp.APSP_EINVAL    # cap < 1
+    assert L.apsp_paths(fake, 16, None, 4, fake, 8, fake, None) == apsp.APSP_EINVAL    # null pairs
+    assert L.apsp_paths(None, 16, None, 0, None, 8, None, None) == apsp.APSP_OK        # nothing to do
 
 
 def test_size_limits_rejected_on_the_host():
