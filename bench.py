@@ -48,7 +48,8 @@ SM_MAX_MHZ = 2070.0
 ALU_PEAK_F32_TFLOPS = 2 * SMS * 64 * SM_MAX_MHZ * 1e6 / 1e12      # 40.27
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "phase3_f32_n8192_bs64.md")
+PROFILE_SUMMARY = {"int": os.path.join(ROOT, "profiles", "phase3_f32_n8192_bs64.md"),
+                   "real": os.path.join(ROOT, "profiles", "phase3_f32_real_n8192_bs64.md")}
 PROFILE_N, PROFILE_BS = 8192, 64  # workload of that capture
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_01201_gb300", "csrc", "fw_minplus_f32.cuh")
 
@@ -112,14 +113,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(n: int, bs: int):
-    """Per-launch DRAM bytes of the phase-3 kernel from the committed ncu summary (captured at
-    n=8192), scaled to this n by the tile count ((n-BS)^2), or None when the summary is missing,
-    the block size differs, or the kernel source changed since the capture."""
+def _traffic_from_profile(n: int, bs: int, kind: str = "int"):
+    """Per-launch DRAM bytes of the phase-3 kernel from the committed ncu summary of the weight
+    kind (captured at n=8192), scaled to this n by the tile count ((n-BS)^2), or None when the
+    summary is missing, the block size differs, or the kernel source changed since the capture."""
     if bs != PROFILE_BS:
         return None
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(PROFILE_SUMMARY[kind]).read()
         src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
@@ -270,8 +271,8 @@ def run_gpu(args, rank: int, world: int):
     roof = {"bound": "alu", "achieved": round(ph3_tflops, 3) if ph3_tflops else None,
             "peak": round(ALU_PEAK_F32_TFLOPS, 2), "unit": "TFLOP/s",
             "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
-            "traffic": _traffic_from_profile(n, args.bs),
-            "kernel": f"fw_phase3_f32_kernel<{args.bs}>",
+            "traffic": _traffic_from_profile(n, args.bs, args.kind),
+            "kernel": f"fw_phase3_f32_kernel<{args.bs}, {'true' if args.kind == 'real' else 'false'}>",
             "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
             "phase_ms_per_step": [round(x / args.steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // args.steps for x in ph_launch]}

@@ -245,17 +245,23 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
           const int2 ent = wq[e];
           const int qi = ent.x >> 8, qj = ent.x & 255;
           const float dn = __int_as_float(ent.y);
+          // eight k-pairs (16 candidates) per step, their loads in flight together
           int kstar = BS;
 #pragma unroll 1
-          for (int kp = 0; kp < BS / 2; ++kp) {
-            const float2 c2 = fadd2_rn(*reinterpret_cast<const float2*>(As + kp * kS2 + 2 * qi),
-                                       *reinterpret_cast<const float2*>(Bs + kp * kS2 + 2 * qj));
-            if (c2.x == dn) {
-              kstar = 2 * kp;
-              break;
+          for (int kp0 = 0; kp0 < BS / 2; kp0 += 8) {
+            float2 c2[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              c2[u] = fadd2_rn(*reinterpret_cast<const float2*>(As + (kp0 + u) * kS2 + 2 * qi),
+                               *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kS2 + 2 * qj));
+            int m = BS;
+#pragma unroll
+            for (int u = 7; u >= 0; --u) {
+              if (c2[u].y == dn) m = 2 * (kp0 + u) + 1;
+              if (c2[u].x == dn) m = 2 * (kp0 + u);
             }
-            if (c2.y == dn) {
-              kstar = 2 * kp + 1;
+            if (m < BS) {
+              kstar = m;
               break;
             }
           }
