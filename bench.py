@@ -132,7 +132,7 @@ def _traffic_from_profile(n: int, bs: int, kind: str = "int"):
     if got.get("kernel_source_sha256_16") != src_hash:
         return None
     try:
-        return float(got["dram_bytes_per_launch"]) * ((n - bs) / (PROFILE_N - PROFILE_BS)) ** 2
+        return float(got["dram_bytes_per_launch"].split()[0]) * ((n - bs) / (PROFILE_N - PROFILE_BS)) ** 2
     except (KeyError, ValueError):
         return None
 
@@ -284,6 +284,10 @@ def run_gpu(args, rank: int, world: int):
             "data": "synthetic", "config": _config(args) | {"parallelism": f"replicas x{world}"},
             "gpu_launches": launches, "roofline": roof, "clocks": clocks}
 
+    # Path reconstruction on the device from the solve's P (before anything overwrites it) (apsp_paths), seeded random pairs.
+    if args.paths > 0:
+        line["paths"] = run_paths(args, dev, P, n, args.paths)
+
     # 16-bit exact path on its workload (n, weights in [1,2]: max_w*(n-1) < 65535).
     if args.u16:
         Wu = inputs.dense_digraph(n, args.seed + 2, 1, 2, device=dev)
@@ -304,10 +308,6 @@ def run_gpu(args, rank: int, world: int):
                          "ms_per_step": round(ums, 3), "dtype_used": "u16x2" if iu.dtype_used == 2 else "f32",
                          "peak_tflops": round(ALU_PEAK_U16_TFLOPS, 2)}
         del Wu, wsu
-
-    # Path reconstruction on the device from the solve's P (apsp_paths), seeded random pairs.
-    if args.paths > 0:
-        line["paths"] = run_paths(args, dev, P, n, args.paths)
 
     # End to end through apsp_fw_host: host pinned W in, host D and P out, every step.
     if args.e2e:
@@ -368,7 +368,7 @@ def run_paths(args, dev, P, n: int, count: int, cap: int = 64, reps: int = 5) ->
     L = lens.to(torch.int64)
     ok = L >= 2
     reads = int((2 * L[ok] - 3).sum())
-    return {"workload": f"{count} random (i, j) pairs of the solved graph, cap {cap}",
+    return {"workload": f"{count} seeded random (i, j) pairs of the timed solve's graph (n={n}), cap {cap}",
             "paths_per_s": round(count / (ms * 1e-3), 1), "ms": round(ms, 4),
             "mean_vertices": round(float(L[ok].float().mean()), 3), "failed": int((L < 0).sum()),
             "same_vertex_pairs": int((L == 1).sum()),

@@ -67,3 +67,23 @@ def test_max_over_ranks_gloo():
     for p in ps:
         p.join(timeout=60)
     assert got == {0: 15.0, 1: 15.0}
+
+
+def test_profile_traffic_parser(tmp_path, monkeypatch):
+    # the summary's value may carry a note after the number; the kernel-source hash gates it
+    sys.path.insert(0, ROOT)
+    import hashlib
+
+    import bench
+    src = tmp_path / "kernel.cuh"
+    src.write_text("// kernel\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    summ = tmp_path / "summary.md"
+    summ.write_text(f"# x\n\n- kernel_source_sha256_16: `{h}`\n- dram_bytes_per_launch: 100.0e6   (mean)\n")
+    monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", {"int": str(summ), "real": str(summ)})
+    scale = ((32768 - 64) / (bench.PROFILE_N - bench.PROFILE_BS)) ** 2
+    assert bench._traffic_from_profile(32768, 64) == pytest.approx(100.0e6 * scale)
+    assert bench._traffic_from_profile(32768, 128) is None          # other block size
+    src.write_text("// changed kernel\n")
+    assert bench._traffic_from_profile(32768, 64, "real") is None   # stale capture
