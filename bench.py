@@ -167,6 +167,23 @@ def cpu_baseline(args) -> dict:
                       f"block of the n={args.n} workload, {dt:.1f} s"}
 
 
+def cpu_parallel_baseline(args) -> dict:
+    """The paper's blocked design on all host cores (OpenMP; oracle/host_blocked.c, bit-exact
+    with the serial oracle), timed on the leading block of the same workload."""
+    from oracle import host_blocked
+    from paper_1811_01201_gb300 import inputs
+    m = args.cpu_par_sample_n
+    W = inputs.dense_digraph(args.n, args.seed, 1, 1000, kind=args.kind, rows=(0, m))[:, :m].contiguous().numpy()
+    host_blocked.build()
+    t0 = time.perf_counter()
+    host_blocked.fw_blocked(W, args.bs)
+    dt = time.perf_counter() - t0
+    return {"value": round(2.0 * m ** 3 / dt / 1e9, 3), "unit": "GFLOPS", "cores": host_blocked.threads(),
+            "kind": "the paper's blocked design on the host cores (OpenMP over blocks, vectorised j loop)",
+            "sample": f"blocked FW (BS={args.bs}) on the leading {m}x{m} block of the n={args.n} workload, "
+                      f"{dt:.1f} s"}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -339,6 +356,7 @@ def run_gpu(args, rank: int, world: int):
 
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_parallel_baseline"] = cpu_parallel_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -574,6 +592,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample-n", type=int, default=2560)
     ap.add_argument("--ref-sample-n", type=int, default=1536)
+    ap.add_argument("--cpu-par-sample-n", type=int, default=4096)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-c2", dest="autotune_c2", action="store_false",
                     help="skip the n=8192 density-0.5 solve with the autotuned block size")

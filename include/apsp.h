@@ -147,7 +147,9 @@ apsp_status apsp_fw_ex(const float* W, float* D, int32_t* P, int n, const apsp_o
  * End-to-end call on HOST buffers: copies W (host, n*n fp32) to the device,
  * runs apsp_fw_ex, copies D and P back to host memory, and synchronises
  * `stream` before returning. W, D, P are host pointers (page-locked memory
- * gives the fastest copies). Device memory is allocated and freed inside.
+ * gives the fastest copies). Device memory is allocated and freed inside:
+ * 8*n*n bytes (W is copied into the device D and solved in place) plus the
+ * workspace apsp_fw_ex would allocate; APSP_ENOMEM if that fails.
  */
 apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
                          apsp_run_info* info, void* stream);

@@ -377,25 +377,23 @@ extern "C" apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n,
   if (n < 1 || !W || !D || !P) return APSP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)n * n * sizeof(float);
-  float *dW = nullptr, *dD = nullptr;
+  // W goes straight into the device D and the solve runs in place (W may alias D).
+  float* dD = nullptr;
   int32_t* dP = nullptr;
-  if (cudaMallocAsync(&dW, bytes, s) != cudaSuccess || cudaMallocAsync(&dD, bytes, s) != cudaSuccess ||
-      cudaMallocAsync(&dP, bytes, s) != cudaSuccess) {
+  if (cudaMallocAsync(&dD, bytes, s) != cudaSuccess || cudaMallocAsync(&dP, bytes, s) != cudaSuccess) {
     cudaGetLastError();
-    if (dW) cudaFreeAsync(dW, s);
     if (dD) cudaFreeAsync(dD, s);
     cudaStreamSynchronize(s);
     return APSP_ENOMEM;
   }
   apsp_status st = APSP_OK;
-  if (cudaMemcpyAsync(dW, W, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) st = APSP_ECUDA;
-  if (st == APSP_OK) st = fw_run(dW, dD, dP, n, opt, nullptr, 0, info, s);
+  if (cudaMemcpyAsync(dD, W, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) st = APSP_ECUDA;
+  if (st == APSP_OK) st = fw_run(dD, dD, dP, n, opt, nullptr, 0, info, s);
   if (st == APSP_OK) {
     if (cudaMemcpyAsync(D, dD, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       st = APSP_ECUDA;
   }
-  cudaFreeAsync(dW, s);
   cudaFreeAsync(dD, s);
   cudaFreeAsync(dP, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st == APSP_OK) st = APSP_ECUDA;
