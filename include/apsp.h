@@ -85,6 +85,14 @@ typedef struct {
  * then synchronises `stream` before returning. */
 #define APSP_FLAG_TIME_PHASES 1
 
+/* APSP_FLAG_TEST_PANEL_TIMEOUT: testing only. Every fp32 phase-3 CTA waits,
+ * with a bound, for the two panel slices it requests by bulk copy; with this
+ * flag it announces the slices but never copies them, so the wait expires
+ * after 20 ms per CTA wave, the CTA leaves its tile untouched and sets the
+ * device fault word that apsp_device_status reports. The results of such a
+ * call are wrong by design; nothing faults or hangs. */
+#define APSP_FLAG_TEST_PANEL_TIMEOUT 0x40000000
+
 /* What a call actually did (optional output). */
 typedef struct {
   int bs_used;       /* block size of the run; the oracle must use the same BS to match P bit-exactly */
@@ -95,6 +103,16 @@ typedef struct {
   int phase_launches[3];
   float phase_ms[3]; /* with APSP_FLAG_TIME_PHASES: device ms in phases 1, 2, 3 (else 0) */
 } apsp_run_info;
+
+/*
+ * Device fault word of the single-graph solver on the current device: a
+ * phase-3 CTA whose bounded wait for its panel slices expired (2 s; a slice
+ * normally arrives within microseconds) sets it and leaves its tile, so the
+ * solve that ran it is wrong. Returns APSP_ETIMEOUT if it is set, else APSP_OK;
+ * clear != 0 resets it. Reflects work that has finished: synchronise the
+ * streams first. apsp_fw_host checks and clears it itself (APSP_ETIMEOUT).
+ */
+apsp_status apsp_device_status(int clear);
 
 /* Library default block size for order n (deterministic in n). */
 int apsp_default_bs(int n);
@@ -115,9 +133,11 @@ const char* apsp_status_str(apsp_status s);
 
 /*
  * Bytes of device workspace apsp_fw_ex needs for (n, opt): always at least
- * 256 (the input scan's counters); n*n-sized working matrices are added when
- * n is not a multiple of 128 or the 16-bit path may be chosen. Returns 0 on
- * invalid arguments (apsp_fw_ex reports them).
+ * 256 (the input scan's counters) plus the packed panel slices of the fp32
+ * path (2 * ceil(n/128) * opt->bs * 528 bytes; opt->bs = 0 means
+ * apsp_default_bs(n)); n*n-sized working matrices are added when n is not a
+ * multiple of 128 or the 16-bit path may be chosen. Returns 0 on invalid
+ * arguments (apsp_fw_ex reports them).
  */
 size_t apsp_fw_workspace_size(int n, const apsp_options* opt);
 
@@ -261,7 +281,8 @@ apsp_status apsp_serve_destroy(apsp_server* s);
  *     (APSP_EINVAL) because it would create CUDA events.
  *   Limit: apsp_fw_workspace_size(n, opt) must not exceed
  *     APSP_NOALLOC_SCRATCH_BYTES, else APSP_ENOMEM and nothing is enqueued.
- *     With dtype F32 that allows any n that is a multiple of 128 and any
+ *     With dtype F32 that allows any n that is a multiple of 128 (up to
+ *     63488 with bs = 128, whose packed panel slices are larger) and any
  *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5760 when n
  *     is a multiple of 128 (room for the 16-bit working matrix).
  *   The first call on a device looks up the array's device address (once per

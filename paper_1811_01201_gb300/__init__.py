@@ -36,6 +36,7 @@ DTYPE_F32 = 1
 DTYPE_U16X2 = 2
 
 FLAG_TIME_PHASES = 1
+FLAG_TEST_PANEL_TIMEOUT = 0x40000000  # testing only: phase-3 panel waits expire (results wrong by design)
 
 
 class ApspError(RuntimeError):
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = True):
     L.apsp_path.restype = c_int
     L.apsp_paths.argtypes = [vp, c_int, vp, c_int, vp, c_int, vp, vp]
     L.apsp_paths.restype = c_int
+    L.apsp_device_status.argtypes = [c_int]
+    L.apsp_device_status.restype = c_int
     if hasattr(L, "apsp_fw_batched"):
         L.apsp_fw_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(c_int), c_int, ctypes.POINTER(apsp_options),
@@ -308,6 +311,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def apsp_device_status(clear: bool = False) -> int:
+    """apsp_device_status: APSP_ETIMEOUT if a phase-3 CTA's bounded wait expired on the current
+    device since the last clear, else APSP_OK. Synchronise the streams that ran solves first."""
+    return int(load().apsp_device_status(1 if clear else 0))
 
 
 def apsp_path(P: np.ndarray | torch.Tensor, i: int, j: int, cap: int | None = None) -> list[int] | None:

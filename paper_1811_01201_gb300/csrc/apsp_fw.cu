@@ -52,6 +52,7 @@ struct PhaseTimer {
   std::vector<cudaEvent_t> ev;
   std::vector<int> tag;
   int launches[3] = {0, 0, 0};
+  int other = 0;  // launches outside the three phases' own kernels (panel packing)
   bool on = false;
   void mark(int phase) {
     if (phase >= 0) ++launches[phase];
@@ -81,10 +82,14 @@ struct PhaseTimer {
 
 // First-wave stagger of the fp32 phase-3 launch (cycles; see the kernel).
 constexpr int kStaggerCycles = 6000;
+// Limit of a phase-3 CTA's wait for its panel slices (they arrive in
+// microseconds), and the short limit used with APSP_FLAG_TEST_PANEL_TIMEOUT.
+constexpr unsigned long long kPanelWaitNs = 2000000000ull;
+constexpr unsigned long long kPanelWaitTestNs = 20000000ull;
 
 template <class T, int BS>
 static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pad, cudaStream_t s, PhaseTimer& tm,
-                                    RoundMax* rm, int graph_int) {
+                                    RoundMax* rm, int graph_int, float* pan, int flags) {
   const int R = n_pad / BS;
   const int nT = n_pad / kTile;
   const size_t ld = (size_t)n_pad;
@@ -106,6 +111,11 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int sms = sm_count();
+  // packed panel slices of the fp32 path: nT A slices, then nT B slices
+  float* Apk = pan;
+  float* Bpk = pan ? pan + (size_t)nT * panel_slice_floats<BS>() : nullptr;
+  const bool test_timeout = (flags & APSP_FLAG_TEST_PANEL_TIMEOUT) != 0;
+  const unsigned long long wait_ns = test_timeout ? kPanelWaitTestNs : kPanelWaitNs;
   tm.mark(-1);
   for (int r = 0; r < R; ++r) {
     fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r, rm);
@@ -114,10 +124,14 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
       fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm);
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value) {
+        fw_pack_panels_f32_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, rm, graph_int, Apk, Bpk);
+        ++tm.other;
         if (graph_int)
-          fw_phase3_f32_kernel<BS, false><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, kStaggerCycles, sms);
+          fw_phase3_f32_kernel<BS, false><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, Apk, Bpk,
+                                                                    kStaggerCycles, sms, wait_ns, test_timeout);
         else
-          fw_phase3_f32_kernel<BS, true><<<nT * nT, 256, sm3r, s>>>(D, P, ld, nT, r, rm, 0, kStaggerCycles, sms);
+          fw_phase3_f32_kernel<BS, true><<<nT * nT, 256, sm3r, s>>>(D, P, ld, nT, r, rm, 0, Apk, Bpk, kStaggerCycles,
+                                                                   sms, wait_ns, test_timeout);
       } else
         fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, kStaggerCycles, sms);
       tm.mark(2);
@@ -128,11 +142,11 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
 
 template <class T>
 static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, int bs, cudaStream_t s,
-                                 PhaseTimer& tm, RoundMax* rm, int graph_int) {
+                                 PhaseTimer& tm, RoundMax* rm, int graph_int, float* pan, int flags) {
   switch (bs) {
-    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm, rm, graph_int);
-    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm, rm, graph_int);
-    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm, rm, graph_int);
+    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
+    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
+    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -142,15 +156,19 @@ static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, 
 struct Plan {
   int n = 0, n_pad = 0, bs = 0, dtype = 0;
   bool in_place = false;
-  size_t ws_stats = 0, ws_d = 0, ws_p = 0, ws_total = 0;  // byte offsets / total
+  size_t ws_stats = 0, ws_d = 0, ws_p = 0, ws_pan = 0, ws_total = 0;  // byte offsets / total
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-// Workspace layout for a given arithmetic: [stats + round maxima][D work][P work].
+// Workspace layout for a given arithmetic and block size:
+// [stats + round maxima][D work][P work][packed panel slices (fp32)].
 constexpr size_t kRoundMaxOffset = 64;  // RoundMax inside the 256-byte head
+static size_t packed_panel_bytes(int n_pad, int bs) {
+  return 2 * (size_t)(n_pad / kTile) * (size_t)(bs / 2) * kS2 * sizeof(float);
+}
 static void layout(Plan& pl, bool p_in_place) {
   const size_t np2 = (size_t)pl.n_pad * pl.n_pad;
   size_t off = 0;
@@ -162,6 +180,8 @@ static void layout(Plan& pl, bool p_in_place) {
   else if (!pl.in_place) off = align256(off + np2 * sizeof(float));
   pl.ws_p = off;
   if (!p_in_place) off = align256(off + np2 * sizeof(int32_t));
+  pl.ws_pan = off;
+  if (pl.dtype == APSP_DTYPE_F32) off = align256(off + packed_panel_bytes(pl.n_pad, pl.bs));
   pl.ws_total = off;
 }
 
@@ -209,6 +229,8 @@ extern "C" size_t apsp_fw_workspace_size(int n, const apsp_options* opt) {
   Plan pl;
   pl.n = n;
   pl.n_pad = padded_order(n);
+  pl.bs = o.bs == 0 ? apsp_default_bs(n) : o.bs;
+  if (!valid_bs(pl.bs)) return 0;
   const bool pad = pl.n_pad != n;
   // F32 working set
   pl.dtype = APSP_DTYPE_F32;
@@ -242,10 +264,11 @@ static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats*
   return APSP_OK;
 }
 
-size_t fw_exec_workspace(int n, int dtype) {
+size_t fw_exec_workspace(int n, int bs, int dtype) {
   Plan pl;
   pl.n = n;
   pl.n_pad = padded_order(n);
+  pl.bs = bs;
   pl.dtype = dtype;
   const bool pad = pl.n_pad != n;
   pl.in_place = (dtype == APSP_DTYPE_F32) && !pad;
@@ -290,7 +313,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
     e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset),
-                            graph_int);
+                            graph_int, reinterpret_cast<float*>(wsb + pl.ws_pan), flags);
     if (e == cudaSuccess && !pl.in_place) {
       copy_out_kernel<float><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;
@@ -299,7 +322,8 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     uint16_t* Dw = reinterpret_cast<uint16_t*>(wsb + pl.ws_d);
     init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
-    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0);
+    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0,
+                            nullptr, flags);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;
@@ -319,7 +343,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     info->dtype_used = dtype;
     info->rounds = pl.n_pad / pl.bs;
     info->n_pad = pl.n_pad;
-    info->launches += aux + tm.launches[0] + tm.launches[1] + tm.launches[2];
+    info->launches += aux + tm.other + tm.launches[0] + tm.launches[1] + tm.launches[2];
     for (int q = 0; q < 3; ++q) {
       info->phase_launches[q] = tm.launches[q];
       info->phase_ms[q] = ms[q];
@@ -372,6 +396,16 @@ extern "C" apsp_status apsp_fw(const float* W, float* D, int32_t* P, int n, void
   return fw_run(W, D, P, n, nullptr, nullptr, 0, nullptr, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" apsp_status apsp_device_status(int clear) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_apsp_fault, sizeof(v)) != cudaSuccess) return APSP_ECUDA;
+  if (clear && v) {
+    const unsigned zero = 0;
+    if (cudaMemcpyToSymbol(g_apsp_fault, &zero, sizeof(zero)) != cudaSuccess) return APSP_ECUDA;
+  }
+  return (v & kFaultPanelCopyTimeout) ? APSP_ETIMEOUT : APSP_OK;
+}
+
 extern "C" apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
                                     apsp_run_info* info, void* stream) {
   if (n < 1 || !W || !D || !P) return APSP_EINVAL;
@@ -397,5 +431,6 @@ extern "C" apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n,
   cudaFreeAsync(dD, s);
   cudaFreeAsync(dP, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st == APSP_OK) st = APSP_ECUDA;
+  if (st == APSP_OK) st = apsp_device_status(1);
   return st;
 }

@@ -14,7 +14,7 @@ int sm_count();
 int padded_order(int n);
 
 // Workspace bytes of fw_exec for a given arithmetic.
-size_t fw_exec_workspace(int n, int dtype);
+size_t fw_exec_workspace(int n, int bs, int dtype);
 
 // Block rounds with the arithmetic already chosen (no input scan; async).
 // graph_int: every finite weight is an integer (enables exact keys in phase 3).

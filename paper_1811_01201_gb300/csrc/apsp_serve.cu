@@ -154,10 +154,10 @@ static void CUDART_CB on_dispatch_done(void* arg) {
   s->cv_done.notify_all();
 }
 
-static size_t job_footprint(int n, bool small, int dtype) {
+static size_t job_footprint(int n, bool small, int bs, int dtype) {
   const size_t nn = (size_t)n * n;
   size_t f = nn * (sizeof(float) + sizeof(int32_t));
-  if (!small) f += fw_exec_workspace(n, dtype);
+  if (!small) f += fw_exec_workspace(n, bs, dtype);
   return f + 4096;
 }
 
@@ -361,7 +361,7 @@ extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n
   const bool eligible = !frac && (double)mx * (double)(n - 1) < 65535.0;
   j->dtype = (!j->small && eligible) ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32;
   j->integral = !frac;
-  j->footprint = job_footprint(n, j->small, j->dtype);
+  j->footprint = job_footprint(n, j->small, j->bs, j->dtype);
   if (j->footprint > s.budget) {
     std::lock_guard<std::mutex> g(s.m);
     ++s.rejected;

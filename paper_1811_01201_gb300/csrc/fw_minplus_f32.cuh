@@ -34,6 +34,10 @@
 // with tx). Both panel slices are stored as k pairs (A transposed), so each
 // 128-bit shared load gives two elements' (a_k, a_k+1) pairs and one PTX
 // add.rn.f32x2 forms two candidates; the min stays one FMNMX per candidate.
+// A small kernel packs every slice of the round once (scaled into keys on
+// keyed rounds); each phase-3 CTA pulls its two slices into shared memory
+// with bulk copies (cp.async.bulk, completion counted on an mbarrier) that run
+// while the CTA loads its tile.
 // Rows/columns of the tile that fall in block r (the panels) are computed but
 // never written.
 #pragma once
@@ -97,7 +101,8 @@ __device__ __forceinline__ float floor_pos(float v) {
 // path's registers alone.
 template <int BS, bool REAL>
 __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __restrict__ P, size_t ld, int kb,
-                                          int r0, int c0, bool keyed_in, float* As, float* Bs, int2* queue) {
+                                          int r0, int c0, bool keyed_in, float* As, float* Bs, int2* queue,
+                                          uint64_t* bar, unsigned long long wait_ns) {
   const bool keyed = REAL ? false : keyed_in;
   constexpr float M = KeyParams<BS>::M;
   const float INF = f32_inf();
@@ -112,37 +117,19 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
     d[a][0] = v0.x; d[a][1] = v0.y; d[a][2] = v0.z; d[a][3] = v0.w;
     d[a][4] = v1.x; d[a][5] = v1.y; d[a][6] = v1.z; d[a][7] = v1.w;
   }
-  const float mb = keyed ? M : 1.f;
-  // B panel slice: rows 2kp and 2kp+1 of one column quad -> two interleaved 128-bit stores
-#pragma unroll
-  for (int m = 0; m < BS / 16; ++m) {
-    const int idx = tid + 256 * m, kp = idx >> 5, q = idx & 31;
-    const float4 x = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp) * ld + c0 + q * 4);
-    const float4 y = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp + 1) * ld + c0 + q * 4);
-    *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
-    *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
-  }
-  // A panel slice: 128 rows x BS columns; a 128-bit load of row i holds k = 4q4..4q4+3, i.e. two
-  // k pairs. Lane -> (row ri = lane & 7 of an 8-row group, column quad cq = lane >> 3).
-#pragma unroll
-  for (int m = 0; m < BS / 8; ++m) {
-    const int idx = tid + 256 * m;
-    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
-    const int i = (grp % (kTile / 8)) * 8 + ri;
-    const int q4 = (grp / (kTile / 8)) * 4 + cq;
-    const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
-    const float k0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
-    const float k1 = keyed ? k0 + 1.f : 0.f, k2 = keyed ? k0 + 2.f : 0.f, k3 = keyed ? k0 + 3.f : 0.f;
-    *reinterpret_cast<float2*>(As + (2 * q4) * kS2 + 2 * i) = make_float2(fmaf(v.x, mb, k0), fmaf(v.y, mb, k1));
-    *reinterpret_cast<float2*>(As + (2 * q4 + 1) * kS2 + 2 * i) = make_float2(fmaf(v.z, mb, k2), fmaf(v.w, mb, k3));
-  }
   if (keyed) {
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int c = 0; c < 8; ++c) d[a][c] *= M;
   }
-  __syncthreads();
+  // The packed panel slices were requested by the kernel before the tile load;
+  // the whole CTA goes on only if every thread saw them arrive in time.
+  if (!__syncthreads_and(mbar_wait_phase0(bar, wait_ns))) {
+    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    mbar_wait_phase0(bar, wait_ns);  // copies still in flight land before the CTA exits
+    return;
+  }
   // Hot loop: per k pair, one f32x2 add and two FMNMX per element.
   const float* Ap = As + ty * 8;
   const float* Bp = Bs + tx * 8;
@@ -366,26 +353,104 @@ __device__ __forceinline__ void spin_cycles(long long cycles) {
   }
 }
 
+// Panel slices of round r in the layout phase 3 reads, written once per round
+// by fw_pack_panels_f32_kernel: slice tr of Apk holds A[i][k] (rows tr*128 ..
+// tr*128+127, the BS columns of block r) at [kp*kS2 + 2i + (k&1)], slice tc of
+// Bpk holds B[k][j] (the BS rows of block r, columns tc*128 ..) at
+// [kp*kS2 + 2j + (k&1)]. On keyed rounds A holds M*a + k + 1 and B holds M*b.
+template <int BS>
+__host__ __device__ constexpr size_t panel_slice_floats() {
+  return (size_t)(BS / 2) * kS2;
+}
+
+template <int BS>
+__device__ __forceinline__ bool round_keyed(const RoundMax* rm, int graph_int) {
+  return graph_int != 0 &&
+         __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
+}
+
+// CTAs 0 .. nT-1 pack the A slices (tile rows), nT .. 2nT-1 the B slices (tile columns).
+template <int BS>
+__global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __restrict__ D, size_t ld, int nT, int r,
+                                                                 const RoundMax* __restrict__ rm, int graph_int,
+                                                                 float* __restrict__ Apk, float* __restrict__ Bpk) {
+  constexpr float M = KeyParams<BS>::M;
+  const bool keyed = round_keyed<BS>(rm, graph_int);
+  const float mb = keyed ? M : 1.f;
+  const int kb = r * BS, tid = threadIdx.x;
+  if ((int)blockIdx.x < nT) {
+    // 128 rows x BS columns; a 128-bit load of row i holds k = 4q4..4q4+3, i.e. two k pairs.
+    // Lane -> (row ri = lane & 7 of an 8-row group, column quad cq = lane >> 3).
+    const int r0 = blockIdx.x * kTile;
+    float* As = Apk + panel_slice_floats<BS>() * blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < BS / 8; ++m) {
+      const int idx = tid + 256 * m;
+      const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
+      const int i = (grp % (kTile / 8)) * 8 + ri;
+      const int q4 = (grp / (kTile / 8)) * 4 + cq;
+      const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
+      const float k0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
+      const float k1 = keyed ? k0 + 1.f : 0.f, k2 = keyed ? k0 + 2.f : 0.f, k3 = keyed ? k0 + 3.f : 0.f;
+      *reinterpret_cast<float2*>(As + (2 * q4) * kS2 + 2 * i) = make_float2(fmaf(v.x, mb, k0), fmaf(v.y, mb, k1));
+      *reinterpret_cast<float2*>(As + (2 * q4 + 1) * kS2 + 2 * i) = make_float2(fmaf(v.z, mb, k2), fmaf(v.w, mb, k3));
+    }
+  } else {
+    // rows 2kp and 2kp+1 of one column quad -> two interleaved 128-bit stores
+    const int tc = blockIdx.x - nT, c0 = tc * kTile;
+    float* Bs = Bpk + panel_slice_floats<BS>() * tc;
+#pragma unroll
+    for (int m = 0; m < BS / 16; ++m) {
+      const int idx = tid + 256 * m, kp = idx >> 5, q = idx & 31;
+      const float4 x = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp) * ld + c0 + q * 4);
+      const float4 y = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp + 1) * ld + c0 + q * 4);
+      *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
+      *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
+    }
+  }
+}
+
 // One launch per round; one CTA per 128x128 tile, two CTAs per SM.
 //   rm:        the round's panel maxima written by phases 1-2
 //   graph_int: every weight of the graph is an integer (so every D value is)
+//   Apk, Bpk:  the round's packed panel slices (fw_pack_panels_f32_kernel)
 //   stagger:   CTAs sms .. 2*sms-1 (the first wave's second half) start this
 //              many cycles late, so the first wave's SMs do not all load their
 //              tiles from HBM at the same instant
+//   wait_ns:   limit of the wait for the panel slices; when it expires the CTA
+//              sets kFaultPanelCopyTimeout in g_apsp_fault and leaves its tile
+//   no_copy:   testing only: announce the slices but never copy them, so the
+//              wait expires (the timeout path, with no copy in flight)
+// A thread issues two bulk copies (the A and B slices of this tile) before the
+// CTA loads its tile, so the copies overlap the tile load.
 template <int BS, bool REAL>
 __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
                                                                size_t ld, int nT, int r, const RoundMax* __restrict__ rm,
-                                                               int graph_int, int stagger, int sms) {
+                                                               int graph_int, const float* __restrict__ Apk,
+                                                               const float* __restrict__ Bpk, int stagger, int sms,
+                                                               unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ uint64_t bar;
   const int kb = r * BS;
   const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
   const int r0 = tr * kTile, c0 = tc * kTile;
   // Tiles entirely inside row band r or column band r belong to phases 1-2.
   if ((r0 >= kb && r0 + kTile <= kb + BS) || (c0 >= kb && c0 + kTile <= kb + BS)) return;
-  const bool keyed = !REAL && graph_int != 0 &&
-                     __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
+  const bool keyed = !REAL && round_keyed<BS>(rm, graph_int);
   if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
-  tile_body<BS, REAL>(D, P, ld, kb, r0, c0, keyed, sm, sm + (BS / 2) * kS2, reinterpret_cast<int2*>(sm + BS * kS2));
+  float* As = sm;
+  float* Bs = sm + panel_slice_floats<BS>();
+  constexpr unsigned slice_bytes = (unsigned)(panel_slice_floats<BS>() * sizeof(float));
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, 2 * slice_bytes);
+    if (!no_copy) {
+      bulk_copy_g2s(As, Apk + panel_slice_floats<BS>() * tr, slice_bytes, &bar);
+      bulk_copy_g2s(Bs, Bpk + panel_slice_floats<BS>() * tc, slice_bytes, &bar);
+    }
+  }
+  tile_body<BS, REAL>(D, P, ld, kb, r0, c0, keyed, As, Bs, reinterpret_cast<int2*>(sm + BS * kS2), &bar, wait_ns);
 }
 
 }  // namespace apsp
