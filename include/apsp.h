@@ -133,11 +133,11 @@ const char* apsp_status_str(apsp_status s);
 
 /*
  * Bytes of device workspace apsp_fw_ex needs for (n, opt): always at least
- * 256 (the input scan's counters) plus the packed panel slices of the fp32
- * path (2 * ceil(n/128) * opt->bs * 528 bytes; opt->bs = 0 means
- * apsp_default_bs(n)); n*n-sized working matrices are added when n is not a
- * multiple of 128 or the 16-bit path may be chosen. Returns 0 on invalid
- * arguments (apsp_fw_ex reports them).
+ * 256 (the input scan's counters) plus the round's packed panel slices
+ * (ceil(n/128) * bs * 1056 bytes on the fp32 path, * 800 on the 16-bit path;
+ * bs = opt->bs, or apsp_default_bs(n) when it is 0); n*n-sized working
+ * matrices are added when n is not a multiple of 128 or the 16-bit path may
+ * be chosen. Returns 0 on invalid arguments (apsp_fw_ex reports them).
  */
 size_t apsp_fw_workspace_size(int n, const apsp_options* opt);
 
@@ -283,7 +283,7 @@ apsp_status apsp_serve_destroy(apsp_server* s);
  *     APSP_NOALLOC_SCRATCH_BYTES, else APSP_ENOMEM and nothing is enqueued.
  *     With dtype F32 that allows any n that is a multiple of 128 (up to
  *     63488 with bs = 128, whose packed panel slices are larger) and any
- *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5760 when n
+ *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5632 when n
  *     is a multiple of 128 (room for the 16-bit working matrix).
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any CUDA

@@ -111,9 +111,9 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int sms = sm_count();
-  // packed panel slices of the fp32 path: nT A slices, then nT B slices
+  // packed panel slices: nT A slices, then nT B slices
   float* Apk = pan;
-  float* Bpk = pan ? pan + (size_t)nT * panel_slice_floats<BS>() : nullptr;
+  float* Bpk = pan + (size_t)nT * panel_slice_floats<BS>();
   const bool test_timeout = (flags & APSP_FLAG_TEST_PANEL_TIMEOUT) != 0;
   const unsigned long long wait_ns = test_timeout ? kPanelWaitTestNs : kPanelWaitNs;
   tm.mark(-1);
@@ -132,8 +132,14 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
         else
           fw_phase3_f32_kernel<BS, true><<<nT * nT, 256, sm3r, s>>>(D, P, ld, nT, r, rm, 0, Apk, Bpk, kStaggerCycles,
                                                                    sms, wait_ns, test_timeout);
-      } else
-        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, kStaggerCycles, sms);
+      } else {
+        uint32_t* Apk16 = reinterpret_cast<uint32_t*>(pan);
+        uint32_t* Bpk16 = Apk16 + (size_t)nT * u16_slice_a_words<BS>();
+        fw_pack_panels_u16_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, Apk16, Bpk16);
+        ++tm.other;
+        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, Apk16, Bpk16, kStaggerCycles, sms,
+                                                           wait_ns, test_timeout);
+      }
       tm.mark(2);
     }
   }
@@ -166,8 +172,10 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // Workspace layout for a given arithmetic and block size:
 // [stats + round maxima][D work][P work][packed panel slices (fp32)].
 constexpr size_t kRoundMaxOffset = 64;  // RoundMax inside the 256-byte head
-static size_t packed_panel_bytes(int n_pad, int bs) {
-  return 2 * (size_t)(n_pad / kTile) * (size_t)(bs / 2) * kS2 * sizeof(float);
+static size_t packed_panel_bytes(int n_pad, int bs, int dtype) {
+  const size_t nT = (size_t)(n_pad / kTile);
+  if (dtype == APSP_DTYPE_U16X2) return nT * (size_t)bs * (kSstA16 + kSstB16) * sizeof(uint32_t);
+  return 2 * nT * (size_t)(bs / 2) * kS2 * sizeof(float);
 }
 static void layout(Plan& pl, bool p_in_place) {
   const size_t np2 = (size_t)pl.n_pad * pl.n_pad;
@@ -181,7 +189,7 @@ static void layout(Plan& pl, bool p_in_place) {
   pl.ws_p = off;
   if (!p_in_place) off = align256(off + np2 * sizeof(int32_t));
   pl.ws_pan = off;
-  if (pl.dtype == APSP_DTYPE_F32) off = align256(off + packed_panel_bytes(pl.n_pad, pl.bs));
+  off = align256(off + packed_panel_bytes(pl.n_pad, pl.bs, pl.dtype));
   pl.ws_total = off;
 }
 
@@ -323,7 +331,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
     e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0,
-                            nullptr, flags);
+                            reinterpret_cast<float*>(wsb + pl.ws_pan), flags);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;

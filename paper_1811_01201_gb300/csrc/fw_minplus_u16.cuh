@@ -21,7 +21,9 @@
 // Tiling: 128 x 128 output tile per CTA of 256 threads; each thread owns 8
 // rows (ty*4+{0..3}, 64+ty*4+{0..3}) x 8 consecutive columns (tx*8 ..), i.e.
 // 8 x 4 packed words. The A panel slice is stored transposed with every value
-// duplicated into both halves of a word; the B panel slice as is.
+// duplicated into both halves of a word; the B panel slice as is. A small
+// kernel packs every slice of the round once; each CTA pulls its two slices
+// with bulk copies while it loads its tile.
 #pragma once
 
 #include "fw_common.cuh"
@@ -35,6 +37,17 @@ constexpr int kSstB16 = kTile / 2 + 4;  // words per B row (two uint16 per word)
 template <int BS>
 constexpr size_t minplus_u16_smem_bytes() {
   return sizeof(uint32_t) * (size_t)BS * (kSstA16 + kSstB16);
+}
+
+// Words of one packed A slice (tile row) and one packed B slice (tile column)
+// in the shared-memory layout of the kernel below.
+template <int BS>
+__host__ __device__ constexpr size_t u16_slice_a_words() {
+  return (size_t)BS * kSstA16;
+}
+template <int BS>
+__host__ __device__ constexpr size_t u16_slice_b_words() {
+  return (size_t)BS * kSstB16;
 }
 
 __device__ __forceinline__ uint32_t vadd16(uint32_t a, uint32_t b) {
@@ -77,12 +90,61 @@ __device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint
   }
 }
 
+// The round's panel slices in the kernel's shared-memory layout, packed once
+// per round: CTAs 0 .. nT-1 write A slice tr (As[k * kSstA16 + i] =
+// dup(D[tr*128 + i][kb + k]), transposed and duplicated into both halves),
+// CTAs nT .. 2nT-1 write B slice tc (Bs[k * kSstB16 + q] = D[kb + k][tc*128 +
+// 2q .. 2q+1]).
+template <int BS>
+__global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t* __restrict__ D, size_t ld, int nT,
+                                                                 int r, uint32_t* __restrict__ Apk,
+                                                                 uint32_t* __restrict__ Bpk) {
+  const int kb = r * BS, tid = threadIdx.x;
+  if ((int)blockIdx.x < nT) {
+    // 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
+    const int r0 = blockIdx.x * kTile;
+    uint32_t* As = Apk + u16_slice_a_words<BS>() * blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < BS / 16; ++m) {
+      const int idx = tid + 256 * m;
+      const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
+      const int i = (grp & 15) * 8 + ri;
+      const int q8 = (grp >> 4) * 4 + cq;
+      const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(r0 + i) * ld + kb + q8 * 8);
+      const uint32_t h[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t lo = h[e] & 0xFFFF, hi = h[e] >> 16;
+        As[(q8 * 8 + 2 * e) * kSstA16 + i] = lo | (lo << 16);
+        As[(q8 * 8 + 2 * e + 1) * kSstA16 + i] = hi | (hi << 16);
+      }
+    }
+  } else {
+    // BS rows x 128 uint16 = 16 uint4 per row.
+    const int tc = blockIdx.x - nT, c0 = tc * kTile;
+    uint32_t* Bs = Bpk + u16_slice_b_words<BS>() * tc;
+#pragma unroll
+    for (int m = 0; m < BS / 16; ++m) {
+      const int idx = tid + 256 * m, k = idx >> 4, q = idx & 15;
+      const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
+      *reinterpret_cast<uint4*>(Bs + k * kSstB16 + q * 4) = v;
+    }
+  }
+}
+
+// One launch per round; one CTA per 128x128 tile. Apk / Bpk: the round's
+// packed slices, pulled into shared memory by two bulk copies while the CTA
+// loads its tile; wait_ns / no_copy as in the fp32 kernel (a wait that
+// expires sets kFaultPanelCopyTimeout and the CTA leaves its tile).
 template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restrict__ D, int32_t* __restrict__ P,
                                                                size_t ld, int nT, int r,
-                                                               const RoundMax* __restrict__ rm, int stagger,
-                                                               int sms) {
+                                                               const RoundMax* __restrict__ rm,
+                                                               const uint32_t* __restrict__ Apk,
+                                                               const uint32_t* __restrict__ Bpk, int stagger, int sms,
+                                                               unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) uint32_t smu[];
+  __shared__ uint64_t bar;
   uint32_t* As = smu;                 // As[k * kSstA16 + i] = dup(D[r0 + i][kb + k])
   uint32_t* Bs = smu + BS * kSstA16;  // Bs[k * kSstB16 + q] = D[kb + k][c0 + 2q .. 2q+1]
 
@@ -101,6 +163,17 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int lane = tid & 31, warp = tid >> 5;
+  constexpr unsigned a_bytes = (unsigned)(u16_slice_a_words<BS>() * sizeof(uint32_t));
+  constexpr unsigned b_bytes = (unsigned)(u16_slice_b_words<BS>() * sizeof(uint32_t));
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar, a_bytes + b_bytes);
+    if (!no_copy) {
+      bulk_copy_g2s(As, Apk + u16_slice_a_words<BS>() * tr, a_bytes, &bar);
+      bulk_copy_g2s(Bs, Bpk + u16_slice_b_words<BS>() * tc, b_bytes, &bar);
+    }
+  }
 
   uint32_t w[8][4], old[8][4];
 #pragma unroll
@@ -110,31 +183,11 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
 #pragma unroll
     for (int q = 0; q < 4; ++q) w[a][q] = old[a][q];
   }
-
-  // B slice: BS rows x 128 uint16 = 16 uint4 per row.
-#pragma unroll
-  for (int m = 0; m < BS / 16; ++m) {
-    const int idx = tid + 256 * m, k = idx >> 4, q = idx & 15;
-    const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
-    *reinterpret_cast<uint4*>(Bs + k * kSstB16 + q * 4) = v;
+  if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
+    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    mbar_wait_phase0(&bar, wait_ns);  // copies still in flight land before the CTA exits
+    return;
   }
-  // A slice: 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
-#pragma unroll
-  for (int m = 0; m < BS / 16; ++m) {
-    const int idx = tid + 256 * m;
-    const int ri = idx & 7, cq = (idx >> 3) & 3, grp = idx >> 5;
-    const int i = (grp & 15) * 8 + ri;
-    const int q8 = (grp >> 4) * 4 + cq;
-    const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(r0 + i) * ld + kb + q8 * 8);
-    const uint32_t h[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const uint32_t lo = h[e] & 0xFFFF, hi = h[e] >> 16;
-      As[(q8 * 8 + 2 * e) * kSstA16 + i] = lo | (lo << 16);
-      As[(q8 * 8 + 2 * e + 1) * kSstA16 + i] = hi | (hi << 16);
-    }
-  }
-  __syncthreads();
 
   if (sat)
     minplus_u16_loop<BS, true>(w, As + ty * 4, Bs + tx * 4);

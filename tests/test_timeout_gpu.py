@@ -36,6 +36,24 @@ def test_expired_panel_wait_is_reported_and_the_context_survives(kind):
     assert apsp.apsp_device_status() == apsp.APSP_OK
 
 
+def test_expired_panel_wait_on_the_16_bit_path():
+    n = 256
+    W = inputs.dense_digraph(n, 33, 1, 2, device=DEV)  # 16-bit eligible
+    D = torch.empty_like(W)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_device_status(clear=True)
+    info = apsp.apsp_fw_ex(W, D, P, bs=64, dtype=apsp.DTYPE_U16X2, flags=apsp.FLAG_TEST_PANEL_TIMEOUT)
+    torch.cuda.synchronize()
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    assert apsp.apsp_device_status(clear=True) == apsp.APSP_ETIMEOUT
+    apsp.apsp_fw_ex(W, D, P, bs=64, dtype=apsp.DTYPE_U16X2)
+    torch.cuda.synchronize()
+    Dr, Pr = oracle.fw_blocked(W.cpu().numpy(), 64)
+    np.testing.assert_array_equal(D.cpu().numpy(), Dr)
+    np.testing.assert_array_equal(P.cpu().numpy(), Pr)
+    assert apsp.apsp_device_status() == apsp.APSP_OK
+
+
 def test_host_entry_point_returns_the_timeout():
     n = 200
     W = inputs.dense_digraph(n, 32, 1, 50)
