@@ -592,7 +592,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample-n", type=int, default=2560)
     ap.add_argument("--ref-sample-n", type=int, default=1536)
-    ap.add_argument("--cpu-par-sample-n", type=int, default=4096)
+    ap.add_argument("--cpu-par-sample-n", type=int, default=6144)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-c2", dest="autotune_c2", action="store_false",
                     help="skip the n=8192 density-0.5 solve with the autotuned block size")
