@@ -599,7 +599,7 @@ def main():
     ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serve"],
                     help="solve: the n=32768 single-graph line (with batched/served extras); "
                          "batched / serve: only that workload, as its own JSON line")
-    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
 

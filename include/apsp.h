@@ -135,7 +135,8 @@ const char* apsp_status_str(apsp_status s);
  * Bytes of device workspace apsp_fw_ex needs for (n, opt): always at least
  * 256 (the input scan's counters) plus the round's packed panel slices
  * (ceil(n/128) * bs * 1056 bytes on the fp32 path, * 800 on the 16-bit path;
- * bs = opt->bs, or apsp_default_bs(n) when it is 0); n*n-sized working
+ * bs = opt->bs, or apsp_default_bs(n) when it is 0) and the packed diagonal
+ * block (8 * bs * (bs + 4) bytes); n*n-sized working
  * matrices are added when n is not a multiple of 128 or the 16-bit path may
  * be chosen. Returns 0 on invalid arguments (apsp_fw_ex reports them).
  */
@@ -282,9 +283,10 @@ apsp_status apsp_serve_destroy(apsp_server* s);
  *   Limit: apsp_fw_workspace_size(n, opt) must not exceed
  *     APSP_NOALLOC_SCRATCH_BYTES, else APSP_ENOMEM and nothing is enqueued.
  *     With dtype F32 that allows any n that is a multiple of 128 (up to
- *     63488 with bs = 128, whose packed panel slices are larger) and any
- *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5632 when n
- *     is a multiple of 128 (room for the 16-bit working matrix).
+ *     63360 with bs = 128, whose packed panel slices are larger) and any
+ *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5632 (5504
+ *     with bs = 128) when n is a multiple of 128 (room for the 16-bit
+ *     working matrix).
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any CUDA
  *   stream capture.

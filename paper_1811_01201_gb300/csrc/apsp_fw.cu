@@ -89,10 +89,11 @@ constexpr unsigned long long kPanelWaitTestNs = 20000000ull;
 
 template <class T, int BS>
 static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pad, cudaStream_t s, PhaseTimer& tm,
-                                    RoundMax* rm, int graph_int, float* pan, int flags) {
+                                    RoundMax* rm, int graph_int, float* pan, void* pdiag, int flags) {
   const int R = n_pad / BS;
   const int nT = n_pad / kTile;
   const size_t ld = (size_t)n_pad;
+  constexpr size_t sm1 = phase1_smem_bytes<T, BS>();
   constexpr size_t sm2 = phase2_smem_bytes<T, BS>();
   constexpr size_t sm3 = std::is_same<T, F32T>::value ? minplus_f32_smem_bytes<BS>() : minplus_u16_smem_bytes<BS>();
   constexpr size_t sm3r = minplus_f32_smem_bytes<BS, true>();
@@ -100,6 +101,9 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
     cudaError_t e1 = cudaFuncSetAttribute(fw_phase2_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    const cudaError_t e0 =
+        cudaFuncSetAttribute(fw_phase1_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e1 == cudaSuccess) e1 = e0;
     cudaError_t e2, e3 = cudaSuccess;
     if constexpr (std::is_same<T, F32T>::value) {
       e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
@@ -117,11 +121,14 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   const bool test_timeout = (flags & APSP_FLAG_TEST_PANEL_TIMEOUT) != 0;
   const unsigned long long wait_ns = test_timeout ? kPanelWaitTestNs : kPanelWaitNs;
   tm.mark(-1);
+  using reg_t = typename T::reg_t;
+  reg_t* pk = static_cast<reg_t*>(pdiag);
   for (int r = 0; r < R; ++r) {
-    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, 0, s>>>(D, P, ld, r, rm);
+    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, sm1, s>>>(D, P, ld, r, rm, pk);
     tm.mark(0);
     if (R > 1) {
-      fw_phase2_kernel<T, BS><<<2 * (R - 1), SeqShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm);
+      fw_phase2_kernel<T, BS><<<2 * (R - 1), LineShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm, pk, wait_ns,
+                                                                          test_timeout);
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value) {
         fw_pack_panels_f32_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, rm, graph_int, Apk, Bpk);
@@ -148,11 +155,11 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
 
 template <class T>
 static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, int bs, cudaStream_t s,
-                                 PhaseTimer& tm, RoundMax* rm, int graph_int, float* pan, int flags) {
+                                 PhaseTimer& tm, RoundMax* rm, int graph_int, float* pan, void* pdiag, int flags) {
   switch (bs) {
-    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
-    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
-    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm, rm, graph_int, pan, flags);
+    case 32: return launch_rounds_bs<T, 32>(D, P, n_pad, s, tm, rm, graph_int, pan, pdiag, flags);
+    case 64: return launch_rounds_bs<T, 64>(D, P, n_pad, s, tm, rm, graph_int, pan, pdiag, flags);
+    case 128: return launch_rounds_bs<T, 128>(D, P, n_pad, s, tm, rm, graph_int, pan, pdiag, flags);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -162,7 +169,7 @@ static cudaError_t launch_rounds(typename T::store_t* D, int32_t* P, int n_pad, 
 struct Plan {
   int n = 0, n_pad = 0, bs = 0, dtype = 0;
   bool in_place = false;
-  size_t ws_stats = 0, ws_d = 0, ws_p = 0, ws_pan = 0, ws_total = 0;  // byte offsets / total
+  size_t ws_stats = 0, ws_d = 0, ws_p = 0, ws_pan = 0, ws_diag = 0, ws_total = 0;  // byte offsets / total
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -170,7 +177,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // Workspace layout for a given arithmetic and block size:
-// [stats + round maxima][D work][P work][packed panel slices (fp32)].
+// [stats + round maxima][D work][P work][packed panel slices][packed diagonal block].
 constexpr size_t kRoundMaxOffset = 64;  // RoundMax inside the 256-byte head
 static size_t packed_panel_bytes(int n_pad, int bs, int dtype) {
   const size_t nT = (size_t)(n_pad / kTile);
@@ -190,6 +197,8 @@ static void layout(Plan& pl, bool p_in_place) {
   if (!p_in_place) off = align256(off + np2 * sizeof(int32_t));
   pl.ws_pan = off;
   off = align256(off + packed_panel_bytes(pl.n_pad, pl.bs, pl.dtype));
+  pl.ws_diag = off;
+  off = align256(off + 2 * (size_t)pl.bs * (pl.bs + 4) * sizeof(uint32_t));
   pl.ws_total = off;
 }
 
@@ -321,7 +330,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
     e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset),
-                            graph_int, reinterpret_cast<float*>(wsb + pl.ws_pan), flags);
+                            graph_int, reinterpret_cast<float*>(wsb + pl.ws_pan), wsb + pl.ws_diag, flags);
     if (e == cudaSuccess && !pl.in_place) {
       copy_out_kernel<float><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;
@@ -331,7 +340,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
     ++aux;
     e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0,
-                            reinterpret_cast<float*>(wsb + pl.ws_pan), flags);
+                            reinterpret_cast<float*>(wsb + pl.ws_pan), wsb + pl.ws_diag, flags);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
       ++aux;

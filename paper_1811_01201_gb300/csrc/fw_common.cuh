@@ -96,6 +96,18 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// shared to global memory; the calling thread then waits until it is done.
+// The shared source must be made visible to the copy engine first
+// (bulk_store_fence after the threads' writes and a barrier).
+__device__ __forceinline__ void bulk_store_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_copy_s2g_and_wait(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Threads and per-thread sub-block of the sequential (phase 1 / phase 2) tile
 // routine: BS x BS tile, each thread owns TE x TE elements.
 template <int BS>

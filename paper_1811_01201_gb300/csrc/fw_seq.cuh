@@ -34,7 +34,9 @@ enum SeqMode { kSeqDiag = 0, kSeqRow = 1, kSeqCol = 2 };
 template <class T, int BS, int MODE>
 __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, int32_t* __restrict__ P, size_t ld,
                                          int kb, int ti0, int tj0, const typename T::reg_t* __restrict__ diag_s,
-                                         typename T::reg_t* rowbuf, typename T::reg_t* colbuf, RoundMax* rm) {
+                                         typename T::reg_t* rowbuf, typename T::reg_t* colbuf, RoundMax* rm,
+                                         typename T::reg_t* __restrict__ pk = nullptr,
+                                         typename T::reg_t* stage = nullptr) {
   using S = SeqShape<BS>;
   using reg_t = typename T::reg_t;
   constexpr int TE = S::TE, TPR = S::TPR, DS = BS + 1;
@@ -94,6 +96,25 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
         P[off] = p[a][c];
       }
     }
+  if (pk != nullptr) {
+    // The finished tile for phase 2 in both of its layouts (see fw_phase2_kernel):
+    // staged in shared memory, then written by two bulk copies.
+    constexpr int PS = BS + 4;
+    constexpr unsigned kBytes = (unsigned)(sizeof(reg_t) * BS * PS);
+#pragma unroll
+    for (int a = 0; a < TE; ++a)
+#pragma unroll
+      for (int c = 0; c < TE; ++c) {
+        stage[(lj0 + c) * PS + li0 + a] = d[a][c];            // row panels: [k][i] = diag[i][k]
+        stage[BS * PS + (li0 + a) * PS + lj0 + c] = d[a][c];  // column panels: [k][j] = diag[k][j]
+      }
+    bulk_store_fence();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_copy_s2g_and_wait(pk, stage, kBytes);
+      bulk_copy_s2g_and_wait(pk + BS * PS, stage + BS * PS, kBytes);
+    }
+  }
   if (rm != nullptr) {
     // Largest value of the finished tile for phase 3's per-round choice: fp32
     // takes the largest finite value (bit pattern) for the exact-key bound;
@@ -118,49 +139,147 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
 }
 
 // Phase 1: the diagonal block of round r (one CTA).
+// pk: receives the finished tile in the two layouts phase 2 copies in
+// (2 * BS * (BS + 4) values), staged in dynamic shared memory of that size.
 template <class T, int BS>
 __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase1_kernel(typename T::store_t* D, int32_t* P, size_t ld,
-                                                                     int r, RoundMax* rm) {
+                                                                     int r, RoundMax* rm, typename T::reg_t* pk) {
   __shared__ typename T::reg_t rowbuf[2 * BS], colbuf[2 * BS];
+  extern __shared__ __align__(16) unsigned char stage_raw[];
   const int kb = r * BS;
   if (rm != nullptr && threadIdx.x == 0) {
     rm->a_bits = 0;  // visible to this CTA's atomics after seq_tile's barriers
     rm->b_bits = 0;
   }
-  seq_tile<T, BS, kSeqDiag>(D, P, ld, kb, kb, kb, nullptr, rowbuf, colbuf, rm);
+  seq_tile<T, BS, kSeqDiag>(D, P, ld, kb, kb, kb, nullptr, rowbuf, colbuf, rm, pk,
+                            reinterpret_cast<typename T::reg_t*>(stage_raw));
+}
+
+template <class T, int BS>
+constexpr size_t phase1_smem_bytes() {
+  return sizeof(typename T::reg_t) * 2 * (size_t)BS * (BS + 4);
 }
 
 // Phase 2: the other blocks of row r (CTAs 0 .. R-2) and of column r
 // (CTAs R-1 .. 2R-3), all against the finished diagonal block.
+//
+// Line owners instead of a barrier per step: in a row-panel block (r, J) the
+// update c = A[i][k] + C[k][j] keeps column j of C to itself (A is the
+// finished diagonal block), and in a column-panel block (I, r) the update
+// c = C[i][k] + B[k][j] keeps row i to itself. Each line (column or row of
+// the block) is held by TPL lanes of one warp, RPT elements each; the lane
+// holding element k of the line passes it to the others with a shuffle, so
+// the BS steps need no block barrier. The diagonal block sits in shared
+// memory, transposed for row panels, so every lane reads its RPT operands of
+// step k as 128-bit loads; phase 1 wrote it in both layouts (pk), and one
+// thread pulls the needed one with a bulk copy while the lanes load their
+// line elements (bounded wait, as in phase 3: wait_ns, no_copy).
+template <int BS>
+struct LineShape {
+  static constexpr int NT = BS == 128 ? 1024 : 256;  // threads per CTA
+  static constexpr int TPL = NT / BS;          // lanes per line
+  static constexpr int RPT = BS / TPL;         // elements per lane
+  static constexpr int LPW = 32 / TPL;         // lines per warp
+  static constexpr int DS = BS + 4;            // shared row stride (16-byte multiple)
+  static_assert(TPL * RPT == BS && LPW * TPL == 32 && RPT % 4 == 0, "bad line shape");
+};
+
 template <class T, int BS>
-__global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase2_kernel(typename T::store_t* D, int32_t* P, size_t ld,
-                                                                     int r, int R, RoundMax* rm) {
+__global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ? 1 : 2)
+    fw_phase2_kernel(typename T::store_t* D, int32_t* P, size_t ld, int r, int R, RoundMax* rm,
+                     const typename T::reg_t* __restrict__ pk, unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
   using reg_t = typename T::reg_t;
-  constexpr int DS = BS + 1;
-  reg_t* diag_s = reinterpret_cast<reg_t*>(smem_raw);
-  reg_t* rowbuf = diag_s + BS * DS;
-  reg_t* colbuf = rowbuf + 2 * BS;
+  using L = LineShape<BS>;
+  constexpr int RPT = L::RPT, DS = L::DS;
+  constexpr unsigned kBytes = (unsigned)(sizeof(reg_t) * BS * DS);
+  reg_t* S = reinterpret_cast<reg_t*>(smem_raw);
   const int kb = r * BS;
-  for (int t = threadIdx.x; t < BS * BS; t += blockDim.x) {
-    const int i = t / BS, j = t % BS;
-    diag_s[i * DS + j] = T::load(D[(size_t)(kb + i) * ld + kb + j]);
-  }
-  __syncthreads();
   const int b = blockIdx.x;
-  if (b < R - 1) {
-    const int J = b < r ? b : b + 1;
-    seq_tile<T, BS, kSeqRow>(D, P, ld, kb, kb, J * BS, diag_s, rowbuf, colbuf, rm);
-  } else {
-    const int bb = b - (R - 1);
-    const int I = bb < r ? bb : bb + 1;
-    seq_tile<T, BS, kSeqCol>(D, P, ld, kb, I * BS, kb, diag_s, rowbuf, colbuf, rm);
+  const bool rowp = b < R - 1;
+  const int bb = rowp ? b : b - (R - 1);
+  const int other = (bb < r ? bb : bb + 1) * BS;  // first column (row panel) or row (column panel)
+  // S[k * DS + x]: A[x][k] = diag[x][k] for row panels, B[k][x] = diag[k][x] for column panels
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, kBytes);
+    if (!no_copy) bulk_copy_g2s(S, pk + (rowp ? 0 : (size_t)BS * DS), kBytes, &bar);
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = lane / L::LPW, jj = lane % L::LPW;
+  const int line = warp * L::LPW + jj;
+  // element e of this lane: row-panel (kb + q*RPT + e, other + line), column-panel (other + line, kb + q*RPT + e)
+  const size_t base = rowp ? (size_t)(kb + q * RPT) * ld + other + line : (size_t)(other + line) * ld + kb + q * RPT;
+  const size_t step = rowp ? ld : 1;
+  reg_t d[RPT];
+  int32_t p[RPT];
+#pragma unroll
+  for (int e = 0; e < RPT; ++e) {
+    d[e] = T::load(D[base + e * step]);
+    p[e] = -1;
+  }
+  if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
+    if (threadIdx.x == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    mbar_wait_phase0(&bar, wait_ns);  // a copy still in flight lands before the CTA exits
+    return;
+  }
+  for (int qo = 0; qo < L::TPL; ++qo) {
+    const int src = qo * L::LPW + jj;
+#pragma unroll
+    for (int kk = 0; kk < RPT; ++kk) {
+      const int k = qo * RPT + kk;
+      const reg_t ck = __shfl_sync(0xffffffffu, d[kk], src);  // element k of this line
+      const reg_t* Sk = S + k * DS + q * RPT;
+#pragma unroll
+      for (int e4 = 0; e4 < RPT; e4 += 4) {
+        reg_t sv[4];
+        if constexpr (std::is_same<reg_t, float>::value) {
+          const float4 v = *reinterpret_cast<const float4*>(Sk + e4);
+          sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+        } else {
+          const uint4 v = *reinterpret_cast<const uint4*>(Sk + e4);
+          sv[0] = v.x; sv[1] = v.y; sv[2] = v.z; sv[3] = v.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const reg_t cand = T::add(sv[u], ck);
+          if (cand < d[e4 + u]) {
+            d[e4 + u] = cand;
+            p[e4 + u] = kb + k;
+          }
+        }
+      }
+    }
+  }
+  unsigned mx = 0;
+#pragma unroll
+  for (int e = 0; e < RPT; ++e) {
+    if (p[e] >= 0) {
+      D[base + e * step] = T::store(d[e]);
+      P[base + e * step] = p[e];
+    }
+    if constexpr (std::is_same<T, F32T>::value) {
+      if (d[e] < f32_inf()) mx = max(mx, (unsigned)__float_as_int(d[e]));
+    } else {
+      mx = max(mx, (unsigned)d[e]);
+    }
+  }
+  // this block's largest value for phase 3's per-round choice (see seq_tile)
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) atomicMax(rowp ? &rm->b_bits : &rm->a_bits, mx);
 }
 
 template <class T, int BS>
 constexpr size_t phase2_smem_bytes() {
-  return sizeof(typename T::reg_t) * ((size_t)BS * (BS + 1) + 4 * BS);
+  return sizeof(typename T::reg_t) * (size_t)BS * LineShape<BS>::DS;
+}
+
+// Values in phase 1's packed output (both layouts).
+template <int BS>
+__host__ __device__ constexpr size_t packed_diag_values() {
+  return 2 * (size_t)BS * LineShape<BS>::DS;
 }
 
 }  // namespace apsp
