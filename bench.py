@@ -48,6 +48,17 @@ SM_MAX_MHZ = 2070.0
 ALU_PEAK_F32_TFLOPS = 2 * SMS * 64 * SM_MAX_MHZ * 1e6 / 1e12      # 40.27
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no measured peak file)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
+
 PROFILE_SUMMARY = {"int": os.path.join(ROOT, "profiles", "phase3_f32_n8192_bs64.md"),
                    "real": os.path.join(ROOT, "profiles", "phase3_f32_real_n8192_bs64.md")}
 PROFILE_N, PROFILE_BS = 8192, 64  # workload of that capture
@@ -293,6 +304,19 @@ def run_gpu(args, rank: int, world: int):
             "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
             "phase_ms_per_step": [round(x / args.steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // args.steps for x in ph_launch]}
+    # Phases 1 and 2 are latency-bound sequential sweeps: their HBM rate against the copy peak.
+    # Algorithmic bytes per tile: BS^2 * (4 read + 4 D write + 4 P write).
+    tile_b = 12.0 * args.bs * args.bs
+    ph12 = {"phase1_us_per_launch": round(ph_ms[0] * 1e3 / max(1, ph_launch[0]), 2),
+            "phase2_us_per_launch": round(ph_ms[1] * 1e3 / max(1, ph_launch[1]), 2),
+            "algorithmic_bytes_per_launch": [tile_b, tile_b * 2 * (R - 1)]}
+    if ph_ms[0] > 0 and ph_ms[1] > 0:
+        g1 = tile_b * ph_launch[0] / (ph_ms[0] * 1e-3) / 1e9
+        g2 = tile_b * 2 * (R - 1) * ph_launch[1] / (ph_ms[1] * 1e-3) / 1e9
+        ph12 |= {"achieved_gbs": [round(g1, 2), round(g2, 1)], "peak_gbs": HBM_PEAK_GBS,
+                 "frac": [round(g1 / HBM_PEAK_GBS, 5), round(g2 / HBM_PEAK_GBS, 4)],
+                 "peak_source": HBM_PEAK_SOURCE}
+    roof["phases_1_2"] = ph12
     clocks = clk.summary()
 
     line = {"metric": "APSP GFLOPS (2n^3/s)", "value": round(value, 2), "unit": "GFLOPS", "n_gpus": world,
