@@ -486,24 +486,30 @@ def run_batched(args, dev, count=4096, seed=6) -> dict:
     flops = sum(2.0 * n ** 3 for n in ns)
     s = torch.cuda.Stream(device=dev)
     b = apsp.Batch(Ws, Ds, Ps, stream=s)
-    with torch.cuda.stream(s):
-        for _ in range(2):
-            b.launch(stream=s)
-    s.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=s):
-        b.launch(stream=s)
     reps = max(3, args.steps)
-    for _ in range(2):
-        graph.replay()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        graph.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    t_b = e0.elapsed_time(e1) / reps * 1e-3
+
+    def time_graph_replays():
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                b.launch(stream=s)
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            b.launch(stream=s)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    t_default = time_graph_replays()   # phase-3 tiles by the size rule
+    rows = b.autotune(stream=s)        # phase-3 tiles timed per size class
+    t_b = time_graph_replays()
     # one library call per graph (async, no validation): the per-graph launch path
     with torch.cuda.stream(s):
         for g in range(count):
@@ -517,6 +523,8 @@ def run_batched(args, dev, count=4096, seed=6) -> dict:
     t_s = time.perf_counter() - t0
     b.close()
     return {"workload": f"{count} dense digraphs, n log-uniform [16,512], integer weights U[1,100], density 0.7",
+            "ph3_tile_rows_by_class": dict(zip(["n<=64", "n<=128", "n<=256", "n<=512"], rows)),
+            "graphs_per_s_size_rule_tiles": round(count / t_default, 1),
             "graphs_per_s": round(count / t_b, 1), "gflops": round(flops / t_b / 1e9, 1),
             "ms_per_batch": round(t_b * 1e3, 3), "launch": "one persistent kernel replayed from a CUDA graph",
             "per_graph_calls": {"graphs_per_s": round(count / t_s, 1), "gflops": round(flops / t_s / 1e9, 1),

@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(c_int), c_int, ctypes.POINTER(apsp_options),
                                         ctypes.POINTER(vp), vp]
         L.apsp_batch_create.restype = c_int
+        L.apsp_batch_autotune.argtypes = [vp, ctypes.POINTER(c_int), vp]
+        L.apsp_batch_autotune.restype = c_int
         L.apsp_batch_launch.argtypes = [vp, vp]
         L.apsp_batch_launch.restype = c_int
         L.apsp_batch_destroy.argtypes = [vp]
@@ -300,6 +302,13 @@ class Batch:
 
     def launch(self, stream=None) -> None:
         _check(load().apsp_batch_launch(self._h, _stream_ptr(stream)), "apsp_batch_launch")
+
+    def autotune(self, stream=None) -> list[int]:
+        """apsp_batch_autotune: time each phase-3 tile height per size class (n <= 64, 128, 256,
+        512) and keep the fastest; returns the chosen heights (0 = no graphs in the class)."""
+        rows = (ctypes.c_int * 4)()
+        _check(load().apsp_batch_autotune(self._h, rows, _stream_ptr(stream)), "apsp_batch_autotune")
+        return [int(x) for x in rows]
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

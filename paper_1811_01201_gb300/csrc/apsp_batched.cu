@@ -15,6 +15,10 @@
 
 namespace apsp {
 
+// Phase-3 tile height of a keyed graph before any autotuning.
+// (the autotuner's choice on the log-uniform [16, 512] mix: 32 rows up to n = 128, 64 above)
+int default_ph3_rows(int n) { return n <= 128 ? 32 : 64; }
+
 // One CTA per graph: count negative / NaN off-diagonal weights.
 __global__ void scan_batch_kernel(const BatchGraph* __restrict__ graphs, int count, unsigned* bad) {
   __shared__ unsigned s_bad;
@@ -48,6 +52,8 @@ struct apsp_batch {
   int ldp = 0;
   size_t smem = 0;
   int grid = 0;
+  std::vector<BatchGraph> hg;  // host copy of the descriptor table
+  std::vector<int> order;      // largest first
 };
 
 extern "C" int apsp_batched_bs(int /*n*/) { return kBBS; }
@@ -77,7 +83,7 @@ extern "C" apsp_status apsp_batch_create(const float* const* W, float* const* D,
   int n_max = 1;
   for (int g = 0; g < count; ++g) {
     if (n[g] < 1 || n[g] > kBMaxN || !W[g] || !D[g] || !P[g]) return APSP_EINVAL;
-    hg[g] = BatchGraph{W[g], D[g], P[g], n[g], 0};
+    hg[g] = BatchGraph{W[g], D[g], P[g], n[g], default_ph3_rows(n[g])};
     n_max = std::max(n_max, n[g]);
   }
   std::vector<int> order(count);
@@ -85,6 +91,8 @@ extern "C" apsp_status apsp_batch_create(const float* const* W, float* const* D,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
 
   apsp_batch* b = new apsp_batch();
+  b->hg = hg;
+  b->order = order;
   b->count = count;
   b->n_max = n_max;
   b->ldp = batched_ldp(n_max);
@@ -134,8 +142,80 @@ extern "C" apsp_status apsp_batch_launch(apsp_batch* b, void* stream) {
   if (!b) return APSP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), s) != cudaSuccess) return APSP_ECUDA;
-  fw_batched_kernel<<<b->grid, kBThreads, b->smem, s>>>(b->d_graphs, b->d_order, b->count, b->d_queue, b->ldp);
+  fw_batched_kernel<<<b->grid, kBThreads, b->smem, s>>>(b->d_graphs, b->d_order, b->count, b->d_queue, b->ldp, 0);
   return cudaGetLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+namespace {
+// Size classes of the phase-3 tile autotuner: n <= 64, <= 128, <= 256, <= 512.
+constexpr int kTuneClasses = 4;
+constexpr int kTuneClassMax[kTuneClasses] = {64, 128, 256, 512};
+constexpr int kTuneRows[3] = {32, 64, 128};
+
+int tune_class(int n) {
+  for (int c = 0; c < kTuneClasses; ++c)
+    if (n <= kTuneClassMax[c]) return c;
+  return kTuneClasses - 1;
+}
+}  // namespace
+
+extern "C" apsp_status apsp_batch_autotune(apsp_batch* b, int* rows_out, void* stream) {
+  if (!b) return APSP_EINVAL;
+  for (const BatchGraph& g : b->hg)
+    if (static_cast<const void*>(g.W) == static_cast<const void*>(g.D)) return APSP_EINVAL;  // reruns need W
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int> cls_order[kTuneClasses];
+  for (int idx : b->order) cls_order[tune_class(b->hg[idx].n)].push_back(idx);  // largest first per class
+  int* d_sub = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  apsp_status st = APSP_OK;
+  if (cudaMalloc(&d_sub, sizeof(int) * b->count) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    st = APSP_ECUDA;
+  int chosen[kTuneClasses] = {0, 0, 0, 0};
+  for (int c = 0; c < kTuneClasses && st == APSP_OK; ++c) {
+    const std::vector<int>& sub = cls_order[c];
+    if (sub.empty()) continue;
+    const int cnt = (int)sub.size();
+    if (cudaMemcpyAsync(d_sub, sub.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = APSP_ECUDA;
+      break;
+    }
+    const int grid = std::min(b->grid, cnt);
+    float best = 0.f;
+    for (int rows : kTuneRows) {
+      float t = 0.f;
+      for (int rep = 0; rep < 3 && st == APSP_OK; ++rep) {  // the first run warms up
+        cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), s);
+        cudaEventRecord(e0, s);
+        fw_batched_kernel<<<grid, kBThreads, b->smem, s>>>(b->d_graphs, d_sub, cnt, b->d_queue, b->ldp, rows);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          st = APSP_ECUDA;
+        if (rep > 0) t += ms;
+      }
+      if (st != APSP_OK) break;
+      if (chosen[c] == 0 || t < best) {
+        best = t;
+        chosen[c] = rows;
+      }
+    }
+  }
+  if (st == APSP_OK) {
+    for (BatchGraph& g : b->hg) g.ph3_rows = chosen[tune_class(g.n)];
+    if (cudaMemcpyAsync(b->d_graphs, b->hg.data(), sizeof(BatchGraph) * b->count, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = APSP_ECUDA;
+  }
+  if (rows_out)
+    for (int c = 0; c < kTuneClasses; ++c) rows_out[c] = chosen[c];
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_sub) cudaFree(d_sub);
+  if (st != APSP_OK) cudaGetLastError();
+  return st;
 }
 
 extern "C" apsp_status apsp_batch_destroy(apsp_batch* b) { return batch_free(b); }
@@ -182,7 +262,7 @@ apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cud
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, smem);
     const int grid = std::max(1, std::min(count, std::max(1, per_sm) * sm_count()));
-    fw_batched_kernel<<<grid, kBThreads, smem, s>>>(d_graphs, d_order, count, d_q, batched_ldp(n_max));
+    fw_batched_kernel<<<grid, kBThreads, smem, s>>>(d_graphs, d_order, count, d_q, batched_ldp(n_max), 0);
     e = cudaGetLastError();
   }
   cudaFreeAsync(buf, s);

@@ -33,7 +33,7 @@ struct BatchGraphDesc {
   float* D;
   int32_t* P;
   int n;
-  int pad;
+  int ph3_rows;  // phase-3 tile height of keyed graphs (0 = the kernel's default)
 };
 
 // Largest graph order of the batched kernel.
@@ -43,5 +43,9 @@ constexpr int kBatchMaxN = 512;
 // points to `count` descriptors followed by `count` ints (the processing
 // order, largest first), all page-locked and alive until the stream passes.
 apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cudaStream_t s);
+
+// Phase-3 tile height the batched kernel uses for a keyed graph of order n
+// unless an autotuning run chose another.
+int default_ph3_rows(int n);
 
 }  // namespace apsp

@@ -184,7 +184,7 @@ static void run_dispatch(ServerImpl* s, Dispatch* d) {
       int* order = reinterpret_cast<int*>(tbl + count);
       for (int g = 0; g < count; ++g) {
         const auto& j = d->jobs[g];
-        tbl[g] = BatchGraphDesc{j->dD, j->dD, j->dP, j->n, 0};
+        tbl[g] = BatchGraphDesc{j->dD, j->dD, j->dP, j->n, default_ph3_rows(j->n)};
         order[g] = g;
       }
       std::stable_sort(order, order + count, [&](int a, int b) { return tbl[a].n > tbl[b].n; });

@@ -19,8 +19,9 @@
 //    update with its path entry. The finished lines are written to global
 //    memory and into the shared panels phase 3 reads.
 //  * phase 3: every element outside row/column band r relaxes through the 32
-//    panel entries (no barriers: the panels are fixed). 4x4 elements per
-//    thread per 64x128 tile.
+//    panel entries (no barriers: the panels are fixed). Keyed graphs use
+//    TR x 128 tiles (TR = 128, 64 or 32, chosen per graph by the host's
+//    autotuner), others 4x4 elements per thread per 64x128 tile.
 //
 // Exact P at one FADD + FMNMX per phase-3 update: for graphs whose weights are
 // all integers and whose longest possible path keeps every key below 2^24,
@@ -45,7 +46,7 @@ struct BatchGraph {
   float* D;
   int32_t* P;
   int n;
-  int keyed_ok;  // host hint unused by the kernel (kept for alignment)
+  int ph3_rows;  // phase-3 tile height on keyed graphs: 128, 64 or 32 (0 = 128); set by the autotuner
 };
 
 struct BatchQueue {
@@ -70,7 +71,9 @@ __device__ __forceinline__ float key_floor(float key) {
   return floor_small(key * (1.f / kBKeyM)) * kBKeyM;
 }
 
-template <bool KEYED>
+// Phase-3 tile of keyed graphs: TR rows x 128 columns, 16 x 32 threads with
+// TR/16 x 4 elements each (TR = 128, 64 or 32).
+template <bool KEYED, int TR>
 __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, int ldp) {
   float* diag = sm;                 // [32][33]
   float* gR = sm + 32 * 33;         // gR[k * kBG + i] = M * diag[i][k] + k + 1   (key form, row-panel lines)
@@ -220,17 +223,18 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
 
     // ---------------- phase 3: every element outside band r
     if (R > 1 && KEYED) {
-      // 16 x 32 threads, 8 x 4 elements each: 128 x 128 tiles; the next tile's
+      // 16 x 32 threads, RA x 4 elements each: TR x 128 tiles; the next tile's
       // elements are loaded while the current one computes
+      constexpr int RA = TR / 16;
       const int ty = tid >> 5, tx = lane;
-      const int tiles_c = (n + 127) / 128;
-      const int ntile = tiles_c * tiles_c;
-      float nxt[8][4];
+      const int tiles_r = (n + TR - 1) / TR, tiles_c = (n + 127) / 128;
+      const int ntile = tiles_r * tiles_c;
+      float nxt[RA][4];
       auto load_tile = [&](int tile) {
         const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
-        const int i0 = tr * 128 + ty * 8, j0 = tc * 128 + tx * 4;
+        const int i0 = tr * TR + ty * RA, j0 = tc * 128 + tx * 4;
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < RA; ++a)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int i = i0 + a, j = j0 + c;
@@ -240,10 +244,10 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
       load_tile(0);
       for (int tile = 0; tile < ntile; ++tile) {
         const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
-        const int i0 = tr * 128 + ty * 8, j0 = tc * 128 + tx * 4;
-        float d[8][4];
+        const int i0 = tr * TR + ty * RA, j0 = tc * 128 + tx * 4;
+        float d[RA][4];
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < RA; ++a)
 #pragma unroll
           for (int c = 0; c < 4; ++c) d[a][c] = nxt[a][c] * kBKeyM;
         if (tile + 1 < ntile) load_tile(tile + 1);
@@ -252,19 +256,29 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           const float* Bp = Bs + j0;
 #pragma unroll 8
           for (int k = 0; k < kBBS; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
-            const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * ldp + 4);
+            float av[RA];
+            if constexpr (RA == 8) {
+              const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
+              const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * ldp + 4);
+              av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+              av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+            } else if constexpr (RA == 4) {
+              const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
+              av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+            } else {
+              const float2 a0 = *reinterpret_cast<const float2*>(Ap + k * ldp);
+              av[0] = a0.x; av[1] = a0.y;
+            }
             const float4 b4 = *reinterpret_cast<const float4*>(Bp + k * ldp);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
               for (int c = 0; c < 4; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
           }
           // slot 0 = unchanged; slot s = improved at k = s-1
 #pragma unroll
-          for (int a = 0; a < 8; ++a)
+          for (int a = 0; a < RA; ++a)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               const int i = i0 + a, j = j0 + c;
@@ -348,9 +362,10 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
 }
 
 // Persistent kernel: each CTA repeatedly takes the next graph (largest first).
+// force_rows != 0 overrides every graph's phase-3 tile height (autotuning runs).
 __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGraph* __restrict__ graphs,
                                                                   const int* __restrict__ order, int count,
-                                                                  BatchQueue* q, int ldp) {
+                                                                  BatchQueue* q, int ldp, int force_rows) {
   extern __shared__ __align__(16) float smb[];
   __shared__ int s_g, s_keyed;
   __shared__ unsigned s_frac, s_max;
@@ -368,16 +383,30 @@ __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGra
     const int n = g.n;
     // initialise D = W (zero diagonal), P = -1; find integrality and the largest finite weight
     unsigned frac = 0, mx = 0;
-    for (size_t t = threadIdx.x; t < (size_t)n * n; t += kBThreads) {
-      const size_t i = t / n, j = t - i * n;
-      float v = g.W[t];
-      if (i == j) v = 0.f;
-      if (v < f32_inf()) {
-        frac |= (v != floorf(v));
-        mx = max(mx, (unsigned)__float_as_int(v));
+    const size_t nn = (size_t)n * n;
+    constexpr int kInitUnroll = 8;  // loads of a thread in flight together
+    for (size_t t0 = threadIdx.x; t0 < nn; t0 += (size_t)kInitUnroll * kBThreads) {
+      float w[kInitUnroll];
+#pragma unroll
+      for (int u = 0; u < kInitUnroll; ++u) {
+        const size_t t = t0 + (size_t)u * kBThreads;
+        w[u] = t < nn ? g.W[t] : 0.f;
       }
-      g.D[t] = v;
-      g.P[t] = -1;
+#pragma unroll
+      for (int u = 0; u < kInitUnroll; ++u) {
+        const size_t t = t0 + (size_t)u * kBThreads;
+        if (t < nn) {
+          const size_t i = t / n, j = t - i * n;
+          float v = w[u];
+          if (i == j) v = 0.f;
+          if (v < f32_inf()) {
+            frac |= (v != floorf(v));
+            mx = max(mx, (unsigned)__float_as_int(v));
+          }
+          g.D[t] = v;
+          g.P[t] = -1;
+        }
+      }
     }
     if (frac) s_frac = 1;
     atomicMax(&s_max, mx);
@@ -388,8 +417,11 @@ __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGra
       s_keyed = (s_frac == 0) && (2.0f * mw * (float)n <= 262000.0f);
     }
     __syncthreads();
-    if (s_keyed) batched_graph<true>(g, smb, ldp);
-    else batched_graph<false>(g, smb, ldp);
+    const int rows = force_rows ? force_rows : g.ph3_rows;
+    if (!s_keyed) batched_graph<false, 128>(g, smb, ldp);
+    else if (rows == 32) batched_graph<true, 32>(g, smb, ldp);
+    else if (rows == 64) batched_graph<true, 64>(g, smb, ldp);
+    else batched_graph<true, 128>(g, smb, ldp);
     if (threadIdx.x == 0) atomicAdd(&q->done, 1u);
     __syncthreads();
   }

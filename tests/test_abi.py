@@ -95,6 +95,7 @@ def test_argument_checks_return_status_without_touching_the_gpu():
     assert L.apsp_fw_ex(None, None, None, 0, ctypes.byref(o), None, 0, None, None) == apsp.APSP_EINVAL
     assert L.apsp_batch_create(None, None, None, None, 0, None, ctypes.byref(vp()), None) == apsp.APSP_EINVAL
     assert L.apsp_batch_launch(None, None) == apsp.APSP_EINVAL
+    assert L.apsp_batch_autotune(None, None, None) == apsp.APSP_EINVAL
     assert L.apsp_serve_create(None, 1 << 30, 4) == apsp.APSP_EINVAL
     h = vp()
     assert L.apsp_serve_create(ctypes.byref(h), 1 << 30, 0) == apsp.APSP_EINVAL

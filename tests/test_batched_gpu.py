@@ -102,6 +102,31 @@ def test_reusable_batch_in_cuda_graph():
     b.close()
 
 
+def test_autotuned_tiles_give_identical_results():
+    # graphs in every size class; the autotuner runs each tile height, then the batch is
+    # relaunched with the chosen ones: all results equal the oracle with BS = 32
+    ns = [20, 50, 64, 65, 100, 128, 129, 200, 256, 257, 400, 512]
+    Ws, Wd, Dd, Pd = _make(ns, 15, density=0.6)
+    b = apsp.Batch(Wd, Dd, Pd)
+    rows = b.autotune()
+    assert len(rows) == 4 and all(r in (32, 64, 128) for r in rows)
+    for Dx in Dd:
+        Dx.fill_(-3.0)
+    b.launch()
+    _check_all(Ws, Dd, Pd)
+    b.close()
+    # classes without graphs report 0; in-place batches cannot be autotuned
+    Ws, Wd, Dd, Pd = _make([30, 40], 16)
+    b = apsp.Batch(Wd, Dd, Pd)
+    assert b.autotune() == [b.autotune()[0], 0, 0, 0] and b.autotune()[0] in (32, 64, 128)
+    b.close()
+    b = apsp.Batch(Wd, Wd, Pd)
+    with pytest.raises(apsp.ApspError) as e:
+        b.autotune()
+    assert e.value.status == apsp.APSP_EINVAL
+    b.close()
+
+
 def test_invalid_batches_rejected():
     Ws, Wd, Dd, Pd = _make([40, 50], 13)
     Wd[1][3, 4] = -2.0
