@@ -128,7 +128,7 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
     tm.mark(0);
     if (R > 1) {
       fw_phase2_kernel<T, BS><<<2 * (R - 1), LineShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm, pk, wait_ns,
-                                                                          test_timeout);
+                                                                          test_timeout, graph_int);
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value) {
         fw_pack_panels_f32_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, rm, graph_int, Apk, Bpk);

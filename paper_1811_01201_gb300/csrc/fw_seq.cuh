@@ -174,6 +174,18 @@ constexpr size_t phase1_smem_bytes() {
 // step k as 128-bit loads; phase 1 wrote it in both layouts (pk), and one
 // thread pulls the needed one with a bulk copy while the lanes load their
 // line elements (bounded wait, as in phase 3: wait_ns, no_copy).
+//
+// Exact keys (fp32, integer-valued graphs): an element is held as
+// M*value + slot (M = 2*BS, slot = local k+1 of its last improvement, 0 for
+// none) and step k forms the candidate key M*diag + M*v_k + k + 1 with one
+// FFMA, so one FMNMX replaces the compare and the two selects: a smaller
+// value wins, and on equal values the older, smaller slot is kept, as the
+// strict '<' requires. The finished diagonal block obeys the triangle
+// inequality, so an element improves only through a line element that has
+// not improved itself; every candidate is therefore at most 2*max(diagonal)
+// + max(initial line), and the keys stay exact below 2^24 when that bound
+// allows. Each warp checks it for its own lines (the diagonal maximum comes
+// from phase 1's round maxima) and runs the key loop or the plain loop.
 template <int BS>
 struct LineShape {
   static constexpr int NT = BS == 128 ? 1024 : 256;  // threads per CTA
@@ -187,7 +199,8 @@ struct LineShape {
 template <class T, int BS>
 __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ? 1 : 2)
     fw_phase2_kernel(typename T::store_t* D, int32_t* P, size_t ld, int r, int R, RoundMax* rm,
-                     const typename T::reg_t* __restrict__ pk, unsigned long long wait_ns, int no_copy) {
+                     const typename T::reg_t* __restrict__ pk, unsigned long long wait_ns, int no_copy,
+                     int graph_int) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   using reg_t = typename T::reg_t;
@@ -225,7 +238,54 @@ __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ?
     mbar_wait_phase0(&bar, wait_ns);  // a copy still in flight lands before the CTA exits
     return;
   }
-  for (int qo = 0; qo < L::TPL; ++qo) {
+  bool keyed = false;
+  if constexpr (std::is_same<T, F32T>::value) {
+    if (graph_int) {
+      constexpr float M = 2.0f * BS;
+      unsigned vc = 0;  // largest finite initial value of this warp's lines (bit order = value order)
+#pragma unroll
+      for (int e = 0; e < RPT; ++e)
+        if (d[e] < f32_inf()) vc = max(vc, (unsigned)__float_as_int(d[e]));
+      vc = __reduce_max_sync(0xffffffffu, vc);
+      const float va = __int_as_float((int)max(rm->a_bits, rm->b_bits));  // >= the diagonal block's largest
+      keyed = (2.0f * va + __int_as_float((int)vc)) * M + BS <= 16777215.0f;
+      if (keyed) {
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) d[e] *= M;  // slot 0
+        for (int qo = 0; qo < L::TPL; ++qo) {
+          const int src = qo * L::LPW + jj;
+#pragma unroll
+          for (int kk = 0; kk < RPT; ++kk) {
+            const int k = qo * RPT + kk;
+            const float ck = __shfl_sync(0xffffffffu, d[kk], src);  // key of element k of this line
+            // M * (its value) + k + 1; an INF key stays INF
+            const float vkp = __fmaf_rn(__fsub_rn(__fadd_rd(ck * (1.f / M), 8388608.f), 8388608.f), M,
+                                        (float)(k + 1));
+            const float* Sk = reinterpret_cast<const float*>(S) + k * DS + q * RPT;
+#pragma unroll
+            for (int e4 = 0; e4 < RPT; e4 += 4) {
+              const float4 v = *reinterpret_cast<const float4*>(Sk + e4);
+              d[e4] = fminf(d[e4], __fmaf_rn(v.x, M, vkp));
+              d[e4 + 1] = fminf(d[e4 + 1], __fmaf_rn(v.y, M, vkp));
+              d[e4 + 2] = fminf(d[e4 + 2], __fmaf_rn(v.z, M, vkp));
+              d[e4 + 3] = fminf(d[e4 + 3], __fmaf_rn(v.w, M, vkp));
+            }
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) {
+          const float key = d[e];
+          if (key < f32_inf()) {
+            const float v = __fsub_rn(__fadd_rd(key * (1.f / M), 8388608.f), 8388608.f);
+            const int sl = (int)__fmaf_rn(-v, M, key);
+            d[e] = v;
+            if (sl != 0) p[e] = kb + sl - 1;
+          }
+        }
+      }
+    }
+  }
+  if (!keyed) for (int qo = 0; qo < L::TPL; ++qo) {
     const int src = qo * L::LPW + jj;
 #pragma unroll
     for (int kk = 0; kk < RPT; ++kk) {
