@@ -7,13 +7,11 @@
 // ascending over block r, every element relaxes through D[i][k] + D[k][j]
 // with a strict '<', and P records the global k (Section 4.2, Section 3).
 //
-// GPU mapping: one CTA per tile; every thread keeps a TE x TE sub-block of the
-// tile in registers. Step k needs row k and/or column k of the tile as they
-// stand after step k-1 (neither changes during step k, because D[k][k] = 0);
-// their owners publish them into a double-buffered shared-memory row/column,
-// so one barrier per step orders the whole update exactly like the serial
-// loop. The fixed operand of a panel tile (the finished diagonal block) sits
-// in shared memory.
+// GPU mapping: phase 1 is one CTA holding the diagonal tile in registers, one
+// barrier per step; phase 2 is one CTA per panel tile, its lines owned by the
+// lanes of a warp, no barrier per step (details at each kernel). Step k needs
+// row k and/or column k as they stand after step k-1; neither changes during
+// step k, because D[k][k] = 0.
 #pragma once
 
 #include <type_traits>
@@ -22,24 +20,22 @@
 
 namespace apsp {
 
-enum SeqMode { kSeqDiag = 0, kSeqRow = 1, kSeqCol = 2 };
-
-// Update one BS x BS tile of D (origin ti0, tj0; leading dimension ld) through
-// the intermediates kb .. kb+BS-1.
-//   kSeqDiag: C = A = B = block (r,r)            c = C[i][k] + C[k][j]
-//   kSeqRow:  C = B = block (r,J), A = diag       c = Diag[i][k] + C[k][j]
-//   kSeqCol:  C = A = block (I,r), B = diag       c = C[i][k] + Diag[k][j]
-// diag_s: BS x (BS+1) shared copy of the finished diagonal block (row and
-// column modes). rowbuf / colbuf: 2*BS shared scratch each.
-template <class T, int BS, int MODE>
-__device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, int32_t* __restrict__ P, size_t ld,
-                                         int kb, int ti0, int tj0, const typename T::reg_t* __restrict__ diag_s,
-                                         typename T::reg_t* rowbuf, typename T::reg_t* colbuf, RoundMax* rm,
-                                         typename T::reg_t* __restrict__ pk = nullptr,
-                                         typename T::reg_t* stage = nullptr) {
+// Phase 1: the diagonal block (kb..kb+BS-1)^2 of round r, updated in place
+// through its own intermediates, c = C[i][k] + C[k][j] with k ascending.
+// Every thread keeps a TE x TE sub-block in registers; the owners of row k
+// and column k publish them into a double-buffered shared row/column, so one
+// barrier per step orders the sweep exactly like the serial loop.
+//
+// (Exact keys, which serve phases 2 and 3, did not pay here: at BS = 32 and
+// 64 this sweep is bound by the barrier and shared-memory round trip of each
+// step, not by its ALU work.)
+template <class T, int BS>
+__device__ __forceinline__ void diag_tile(typename T::store_t* __restrict__ D, int32_t* __restrict__ P, size_t ld,
+                                          int kb, typename T::reg_t* rowbuf, typename T::reg_t* colbuf, RoundMax* rm,
+                                          typename T::reg_t* __restrict__ pk, typename T::reg_t* stage) {
   using S = SeqShape<BS>;
   using reg_t = typename T::reg_t;
-  constexpr int TE = S::TE, TPR = S::TPR, DS = BS + 1;
+  constexpr int TE = S::TE, TPR = S::TPR;
   const int tid = threadIdx.x, tx = tid % TPR, ty = tid / TPR;
   const int li0 = ty * TE, lj0 = tx * TE;
 
@@ -49,7 +45,7 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
   for (int a = 0; a < TE; ++a)
 #pragma unroll
     for (int c = 0; c < TE; ++c) {
-      d[a][c] = T::load(D[(size_t)(ti0 + li0 + a) * ld + tj0 + lj0 + c]);
+      d[a][c] = T::load(D[(size_t)(kb + li0 + a) * ld + kb + lj0 + c]);
       p[a][c] = -1;
     }
 
@@ -59,20 +55,20 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
       const int k = k0 + kk;
       reg_t* rb = rowbuf + (k & 1) * BS;
       reg_t* cb = colbuf + (k & 1) * BS;
-      if (MODE != kSeqCol && ty == k0 / TE) {
+      if (ty == k0 / TE) {
 #pragma unroll
         for (int c = 0; c < TE; ++c) rb[lj0 + c] = d[kk][c];
       }
-      if (MODE != kSeqRow && tx == k0 / TE) {
+      if (tx == k0 / TE) {
 #pragma unroll
         for (int a = 0; a < TE; ++a) cb[li0 + a] = d[a][kk];
       }
       __syncthreads();
       reg_t av[TE], bv[TE];
 #pragma unroll
-      for (int a = 0; a < TE; ++a) av[a] = (MODE == kSeqRow) ? diag_s[(li0 + a) * DS + k] : cb[li0 + a];
+      for (int a = 0; a < TE; ++a) av[a] = cb[li0 + a];
 #pragma unroll
-      for (int c = 0; c < TE; ++c) bv[c] = (MODE == kSeqCol) ? diag_s[k * DS + lj0 + c] : rb[lj0 + c];
+      for (int c = 0; c < TE; ++c) bv[c] = rb[lj0 + c];
 #pragma unroll
       for (int a = 0; a < TE; ++a)
 #pragma unroll
@@ -90,13 +86,13 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
   for (int a = 0; a < TE; ++a)
 #pragma unroll
     for (int c = 0; c < TE; ++c) {
-      const size_t off = (size_t)(ti0 + li0 + a) * ld + tj0 + lj0 + c;
+      const size_t off = (size_t)(kb + li0 + a) * ld + kb + lj0 + c;
       if (p[a][c] >= 0) {
         D[off] = T::store(d[a][c]);
         P[off] = p[a][c];
       }
     }
-  if (pk != nullptr) {
+  {
     // The finished tile for phase 2 in both of its layouts (see fw_phase2_kernel):
     // staged in shared memory, then written by two bulk copies.
     constexpr int PS = BS + 4;
@@ -115,30 +111,27 @@ __device__ __forceinline__ void seq_tile(typename T::store_t* __restrict__ D, in
       bulk_copy_s2g_and_wait(pk + BS * PS, stage + BS * PS, kBytes);
     }
   }
-  if (rm != nullptr) {
-    // Largest value of the finished tile for phase 3's per-round choice: fp32
-    // takes the largest finite value (bit pattern) for the exact-key bound;
-    // 16-bit takes the largest value including INF for the overflow test.
-    unsigned mx = 0;
+  // Largest value of the finished tile for phase 3's per-round choice: fp32
+  // takes the largest finite value (bit pattern) for the exact-key bound;
+  // 16-bit takes the largest value including INF for the overflow test.
+  unsigned mx = 0;
 #pragma unroll
-    for (int a = 0; a < TE; ++a)
+  for (int a = 0; a < TE; ++a)
 #pragma unroll
-      for (int c = 0; c < TE; ++c) {
-        if constexpr (std::is_same<T, F32T>::value) {
-          if (d[a][c] < f32_inf()) mx = max(mx, (unsigned)__float_as_int(d[a][c]));
-        } else {
-          mx = max(mx, (unsigned)d[a][c]);
-        }
+    for (int c = 0; c < TE; ++c) {
+      if constexpr (std::is_same<T, F32T>::value) {
+        if (d[a][c] < f32_inf()) mx = max(mx, (unsigned)__float_as_int(d[a][c]));
+      } else {
+        mx = max(mx, (unsigned)d[a][c]);
       }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if ((threadIdx.x & 31) == 0) {
-      if (MODE != kSeqRow) atomicMax(&rm->a_bits, mx);
-      if (MODE != kSeqCol) atomicMax(&rm->b_bits, mx);
     }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&rm->a_bits, mx);
+    atomicMax(&rm->b_bits, mx);
   }
 }
 
-// Phase 1: the diagonal block of round r (one CTA).
 // pk: receives the finished tile in the two layouts phase 2 copies in
 // (2 * BS * (BS + 4) values), staged in dynamic shared memory of that size.
 template <class T, int BS>
@@ -147,12 +140,11 @@ __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase1_kernel(typename T:
   __shared__ typename T::reg_t rowbuf[2 * BS], colbuf[2 * BS];
   extern __shared__ __align__(16) unsigned char stage_raw[];
   const int kb = r * BS;
-  if (rm != nullptr && threadIdx.x == 0) {
-    rm->a_bits = 0;  // visible to this CTA's atomics after seq_tile's barriers
+  if (threadIdx.x == 0) {
+    rm->a_bits = 0;  // visible to this CTA's atomics after the tile's barriers
     rm->b_bits = 0;
   }
-  seq_tile<T, BS, kSeqDiag>(D, P, ld, kb, kb, kb, nullptr, rowbuf, colbuf, rm, pk,
-                            reinterpret_cast<typename T::reg_t*>(stage_raw));
+  diag_tile<T, BS>(D, P, ld, kb, rowbuf, colbuf, rm, pk, reinterpret_cast<typename T::reg_t*>(stage_raw));
 }
 
 template <class T, int BS>
@@ -326,7 +318,7 @@ __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ?
       mx = max(mx, (unsigned)d[e]);
     }
   }
-  // this block's largest value for phase 3's per-round choice (see seq_tile)
+  // this block's largest value for phase 3's per-round choice (see diag_tile)
   mx = __reduce_max_sync(0xffffffffu, mx);
   if (lane == 0) atomicMax(rowp ? &rm->b_bits : &rm->a_bits, mx);
 }
