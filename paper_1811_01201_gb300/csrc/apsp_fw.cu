@@ -80,6 +80,25 @@ struct PhaseTimer {
 
 // ---------------------------------------------------------------- launch tables
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while its predecessor in the stream still runs; it waits for it in
+// pdl_prologue (every round kernel starts with that).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                    cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // First-wave stagger of the fp32 phase-3 launch (cycles; see the kernel).
 constexpr int kStaggerCycles = 6000;
 // Limit of a phase-3 CTA's wait for its panel slices (they arrive in
@@ -123,33 +142,43 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   tm.mark(-1);
   using reg_t = typename T::reg_t;
   reg_t* pk = static_cast<reg_t*>(pdiag);
-  for (int r = 0; r < R; ++r) {
-    fw_phase1_kernel<T, BS><<<1, SeqShape<BS>::NT, sm1, s>>>(D, P, ld, r, rm, pk);
+  cudaError_t err = cudaSuccess;
+  auto keep = [&err](cudaError_t e) {
+    if (err == cudaSuccess) err = e;
+  };
+  for (int r = 0; r < R && err == cudaSuccess; ++r) {
+    keep(launch_dependent(fw_phase1_kernel<T, BS>, 1, SeqShape<BS>::NT, sm1, s, D, P, ld, r, rm, pk));
     tm.mark(0);
     if (R > 1) {
-      fw_phase2_kernel<T, BS><<<2 * (R - 1), LineShape<BS>::NT, sm2, s>>>(D, P, ld, r, R, rm, pk, wait_ns,
-                                                                          test_timeout, graph_int);
+      keep(launch_dependent(fw_phase2_kernel<T, BS>, 2 * (R - 1), LineShape<BS>::NT, sm2, s, D, P, ld, r, R, rm,
+                       static_cast<const reg_t*>(pk), wait_ns, (int)test_timeout, graph_int));
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value) {
-        fw_pack_panels_f32_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, rm, graph_int, Apk, Bpk);
+        keep(launch_dependent(fw_pack_panels_f32_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const float*>(D), ld, nT, r,
+                         static_cast<const RoundMax*>(rm), graph_int, Apk, Bpk));
         ++tm.other;
         if (graph_int)
-          fw_phase3_f32_kernel<BS, false><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, graph_int, Apk, Bpk,
-                                                                    kStaggerCycles, sms, wait_ns, test_timeout);
+          keep(launch_dependent(fw_phase3_f32_kernel<BS, false>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
+                           static_cast<const RoundMax*>(rm), graph_int, static_cast<const float*>(Apk),
+                           static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
         else
-          fw_phase3_f32_kernel<BS, true><<<nT * nT, 256, sm3r, s>>>(D, P, ld, nT, r, rm, 0, Apk, Bpk, kStaggerCycles,
-                                                                   sms, wait_ns, test_timeout);
+          keep(launch_dependent(fw_phase3_f32_kernel<BS, true>, nT * nT, 256, sm3r, s, D, P, ld, nT, r,
+                           static_cast<const RoundMax*>(rm), 0, static_cast<const float*>(Apk),
+                           static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
       } else {
         uint32_t* Apk16 = reinterpret_cast<uint32_t*>(pan);
         uint32_t* Bpk16 = Apk16 + (size_t)nT * u16_slice_a_words<BS>();
-        fw_pack_panels_u16_kernel<BS><<<2 * nT, 256, 0, s>>>(D, ld, nT, r, Apk16, Bpk16);
+        keep(launch_dependent(fw_pack_panels_u16_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const uint16_t*>(D), ld, nT,
+                         r, Apk16, Bpk16));
         ++tm.other;
-        fw_phase3_u16_kernel<BS><<<nT * nT, 256, sm3, s>>>(D, P, ld, nT, r, rm, Apk16, Bpk16, kStaggerCycles, sms,
-                                                           wait_ns, test_timeout);
+        keep(launch_dependent(fw_phase3_u16_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
+                         static_cast<const RoundMax*>(rm), static_cast<const uint32_t*>(Apk16),
+                         static_cast<const uint32_t*>(Bpk16), kStaggerCycles, sms, wait_ns, (int)test_timeout));
       }
       tm.mark(2);
     }
   }
+  if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }
 

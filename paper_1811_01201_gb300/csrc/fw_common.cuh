@@ -108,6 +108,17 @@ __device__ __forceinline__ void bulk_copy_s2g_and_wait(void* dst, const void* sr
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
+// Programmatic dependent launch: the round's kernels are launched so that the
+// next one may be scheduled while this one runs. Each kernel first lets its
+// dependent be scheduled (once every CTA of this grid has started or exited),
+// then waits until its own predecessor has completed and its writes are
+// visible, before touching any data. Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Threads and per-thread sub-block of the sequential (phase 1 / phase 2) tile
 // routine: BS x BS tile, each thread owns TE x TE elements.
 template <int BS>

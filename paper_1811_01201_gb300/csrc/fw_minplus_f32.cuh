@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
                                                                  const RoundMax* __restrict__ rm, int graph_int,
                                                                  float* __restrict__ Apk, float* __restrict__ Bpk) {
   constexpr float M = KeyParams<BS>::M;
+  pdl_prologue();
   const bool keyed = round_keyed<BS>(rm, graph_int);
   const float mb = keyed ? M : 1.f;
   const int kb = r * BS, tid = threadIdx.x;
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
                                                                unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) float sm[];
   __shared__ uint64_t bar;
+  pdl_prologue();
   const int kb = r * BS;
   const int tr = blockIdx.x / nT, tc = blockIdx.x - tr * nT;
   const int r0 = tr * kTile, c0 = tc * kTile;

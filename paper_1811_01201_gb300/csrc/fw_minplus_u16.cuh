@@ -99,6 +99,7 @@ template <int BS>
 __global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t* __restrict__ D, size_t ld, int nT,
                                                                  int r, uint32_t* __restrict__ Apk,
                                                                  uint32_t* __restrict__ Bpk) {
+  pdl_prologue();
   const int kb = r * BS, tid = threadIdx.x;
   if ((int)blockIdx.x < nT) {
     // 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
                                                                unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) uint32_t smu[];
   __shared__ uint64_t bar;
+  pdl_prologue();
   uint32_t* As = smu;                 // As[k * kSstA16 + i] = dup(D[r0 + i][kb + k])
   uint32_t* Bs = smu + BS * kSstA16;  // Bs[k * kSstB16 + q] = D[kb + k][c0 + 2q .. 2q+1]
 

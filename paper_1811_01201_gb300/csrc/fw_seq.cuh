@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(SeqShape<BS>::NT) fw_phase1_kernel(typename T:
                                                                      int r, RoundMax* rm, typename T::reg_t* pk) {
   __shared__ typename T::reg_t rowbuf[2 * BS], colbuf[2 * BS];
   extern __shared__ __align__(16) unsigned char stage_raw[];
+  pdl_prologue();
   const int kb = r * BS;
   if (threadIdx.x == 0) {
     rm->a_bits = 0;  // visible to this CTA's atomics after the tile's barriers
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ?
   constexpr int RPT = L::RPT, DS = L::DS;
   constexpr unsigned kBytes = (unsigned)(sizeof(reg_t) * BS * DS);
   reg_t* S = reinterpret_cast<reg_t*>(smem_raw);
+  pdl_prologue();
   const int kb = r * BS;
   const int b = blockIdx.x;
   const bool rowp = b < R - 1;

@@ -190,6 +190,30 @@ def test_in_place_and_workspace():
     _expect_exact(W2, D2.cpu().numpy(), P2.cpu().numpy(), 64)
 
 
+def test_solve_captured_in_a_cuda_graph():
+    # validate = 0 with a caller workspace: fully asynchronous, so the whole solve (every
+    # round's kernels, launched as programmatic dependents) can be captured and replayed
+    n = 384
+    W = inputs.dense_digraph(n, seed=14, lo=1, hi=500, density=0.6)
+    Wd = W.to(DEV)
+    D = torch.empty_like(Wd)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    ws = torch.empty(apsp.apsp_fw_workspace_size(n, bs=64, dtype=apsp.DTYPE_F32), dtype=torch.uint8, device=DEV)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        apsp.apsp_fw_ex(Wd, D, P, bs=64, dtype=apsp.DTYPE_F32, validate=False, workspace=ws, stream=s)
+    D.fill_(-1.0)
+    P.fill_(7)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    Dr, Pr = oracle.fw_blocked(W.numpy(), 64)
+    np.testing.assert_array_equal(D.cpu().numpy(), Dr)
+    np.testing.assert_array_equal(P.cpu().numpy(), Pr)
+
+
 def test_default_entry_point_and_stream():
     n = 333
     W = inputs.dense_digraph(n, seed=13, lo=1, hi=1000, density=0.7)
