@@ -383,19 +383,28 @@ class Server:
                "apsp_serve_submit")
         return int(jid.value)
 
-    def poll(self, job_id: int, n: int, timeout_ms: int = -1, want_result: bool = True):
-        """Returns (D, P, bs_used) as numpy arrays, or raises ApspError (EBUSY/ETIMEOUT while pending)."""
-        D = np.empty((n, n), np.float32) if want_result else None
-        P = np.empty((n, n), np.int32) if want_result else None
+    def poll(self, job_id: int, n: int, timeout_ms: int = -1, want_result: bool = True, out=None):
+        """Returns (D, P, bs_used) as numpy arrays, or raises ApspError (EBUSY/ETIMEOUT while pending).
+        out: optional (D, P) pair of C-contiguous numpy arrays (float32, int32) of n*n elements to
+        receive the result, so that a caller polling many jobs reuses its buffers."""
+        if want_result and out is not None:
+            D, P = out
+            if not (isinstance(D, np.ndarray) and isinstance(P, np.ndarray) and D.dtype == np.float32
+                    and P.dtype == np.int32 and D.size == n * n and P.size == n * n
+                    and D.flags.c_contiguous and P.flags.c_contiguous):
+                raise ValueError("out must be C-contiguous float32 and int32 arrays of n*n elements")
+        else:
+            D = np.empty((n, n), np.float32) if want_result else None
+            P = np.empty((n, n), np.int32) if want_result else None
         bs = ctypes.c_int(0)
         st = load().apsp_serve_poll(self._h, int(job_id), D.ctypes.data if D is not None else None,
                                     P.ctypes.data if P is not None else None, ctypes.byref(bs), int(timeout_ms))
         _check(st, "apsp_serve_poll")
         return D, P, int(bs.value)
 
-    def try_poll(self, job_id: int, n: int, timeout_ms: int = 0, want_result: bool = True):
+    def try_poll(self, job_id: int, n: int, timeout_ms: int = 0, want_result: bool = True, out=None):
         try:
-            return self.poll(job_id, n, timeout_ms, want_result)
+            return self.poll(job_id, n, timeout_ms, want_result, out)
         except ApspError as e:
             if e.status in (APSP_EBUSY, APSP_ETIMEOUT):
                 return None

@@ -55,6 +55,23 @@ def test_mixed_stream_matches_alone_and_oracle():
             np.testing.assert_array_equal(P, Pr)
 
 
+def test_poll_into_reused_buffers():
+    Ws = _graphs(12, 24)
+    bufD = np.empty(1024 * 1024, np.float32)
+    bufP = np.empty(1024 * 1024, np.int32)
+    with apsp.Server(2 << 30, max_slots=8) as srv:
+        ids = [srv.submit(W) for W in Ws]
+        for j, W in zip(ids, Ws):
+            n = W.shape[0]
+            D, P, bs = srv.poll(j, n, timeout_ms=60000, out=(bufD[:n * n].reshape(n, n), bufP[:n * n].reshape(n, n)))
+            assert np.shares_memory(D, bufD) and np.shares_memory(P, bufP)
+            Dr, Pr = oracle.fw_blocked(W, bs)
+            np.testing.assert_array_equal(D, Dr)
+            np.testing.assert_array_equal(P, Pr)
+        with pytest.raises(ValueError):
+            srv.poll(srv.submit(Ws[0]), Ws[0].shape[0], out=(bufD[:10], bufP[:10]))
+
+
 def test_concurrent_submitters_and_overlap():
     Ws = _graphs(60, 22, n_hi=512)
     out = {}
