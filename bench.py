@@ -444,7 +444,8 @@ def run_extra(args, rank: int, world: int):
             line = {"metric": "APSP graphs/s (4096 graphs, n log-uniform in [16,512])", "value": r["graphs_per_s"],
                     "unit": "graphs/s", "gflops": r["gflops"]}
         else:
-            r = run_serve(args, dev, args.serve_seconds if args.serve_seconds > 0 else 60.0)
+            r = run_serve(args, dev, args.serve_seconds if args.serve_seconds > 0 else 60.0,
+                          sweep_fracs=(0.5, 0.95, 1.1) if args.serve_sweep else None)
             line = {"metric": "APSP served graphs/s at 80% of saturation", "value": r["graphs_per_s"],
                     "unit": "graphs/s", "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"]}
     line.update({"n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -543,7 +544,8 @@ def run_batched(args, dev, count=4096, seed=6) -> dict:
             "speedup_vs_per_graph": round(t_s / t_b, 2)}
 
 
-def run_serve(args, dev, seconds: float, seed=7, pool_size=512, clients=4) -> dict:
+def run_serve(args, dev, seconds: float, seed=7, pool_size=512, clients=4, sweep_fracs=None,
+              sweep_seconds=15.0) -> dict:
     """Poisson stream of requests, n = clip(round(lognormal(ln 256, 1.0)), 32, 4096), integer
     weights U[1,64]; arrival rate 80% of the measured saturation throughput. Requests come from
     `clients` submitting threads (each a Poisson stream of rate/clients) and results are copied
@@ -602,6 +604,18 @@ def run_serve(args, dev, seconds: float, seed=7, pool_size=512, clients=4) -> di
         el, cnt = drive(srv, arr)
         st = srv.stats()
     flops = sum(2.0 * pool[(c * 7919 + i) % pool_size].shape[0] ** 3 for c in range(clients) for i in range(per))
+    sweep = []
+    for frac in (sweep_fracs or ()):
+        # the same stream at other arrival rates (fractions of the measured saturation), shorter runs
+        r_x = frac * sat
+        per_x = max(1, int(r_x * sweep_seconds) // clients)
+        arr_x = [inputs.poisson_arrivals(per_x, seed * 100 + 50 + c, r_x / clients) for c in range(clients)]
+        with apsp.Server(budget, max_slots=512) as srv:
+            el_x, cnt_x = drive(srv, arr_x)
+            st_x = srv.stats()
+        sweep.append({"load": frac, "arrival_rate_per_s": round(r_x, 1), "graphs_per_s": round(cnt_x / el_x, 1),
+                      "p50_ms": round(st_x.p50_ms, 3), "p99_ms": round(st_x.p99_ms, 3),
+                      "max_ms": round(st_x.max_ms, 3), "seconds": round(el_x, 2)})
     # the same request mix solved one at a time through the single-graph host call
     seq_n = min(64, pool_size)
     bufD = torch.empty(n_max * n_max)
@@ -619,6 +633,7 @@ def run_serve(args, dev, seconds: float, seed=7, pool_size=512, clients=4) -> di
             "gflops": round(flops / el / 1e9, 1), "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
             "max_ms": round(st.max_ms, 3), "hbm_peak_gib": round(st.hbm_peak / 2 ** 30, 3),
             "one_at_a_time_graphs_per_s": round(seq_gps, 1),
+            **({"load_sweep": sweep} if sweep else {}),
             "speedup_vs_one_at_a_time": round(sat / seq_gps, 2)}
 
 
@@ -648,6 +663,8 @@ def main():
                     help="solve: the n=32768 single-graph line (with batched/served extras); "
                          "batched / serve: only that workload, as its own JSON line")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="with --workload serve: also 15 s runs at 50%%, 95%% and 110%% of saturation")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
 
