@@ -178,7 +178,8 @@ constexpr size_t phase1_smem_bytes() {
 // not improved itself; every candidate is therefore at most 2*max(diagonal)
 // + max(initial line), and the keys stay exact below 2^24 when that bound
 // allows. Each warp checks it for its own lines (the diagonal maximum comes
-// from phase 1's round maxima) and runs the key loop or the plain loop.
+// from phase 1's round maxima) and runs the key loop or the plain loop. On
+// the 16-bit path the keys are 32-bit integers and always exact.
 template <int BS>
 struct LineShape {
   static constexpr int NT = BS == 128 ? 1024 : 256;  // threads per CTA
@@ -278,6 +279,39 @@ __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ?
         }
       }
     }
+  }
+  if constexpr (std::is_same<T, U16T>::value) {
+    // 16-bit path: keys M*v + slot in 32-bit integers are always exact (v <= 0xFFFF). A
+    // candidate through an INF (0xFFFF) operand is at least M*0xFFFF + k + 1, above the key of
+    // any value up to INF with an older slot, so it never wins, as the saturating sum never did.
+    constexpr uint32_t M = 2 * BS;
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) d[e] *= M;  // slot 0
+    for (int qo = 0; qo < L::TPL; ++qo) {
+      const int src = qo * L::LPW + jj;
+#pragma unroll
+      for (int kk = 0; kk < RPT; ++kk) {
+        const int k = qo * RPT + kk;
+        const uint32_t ck = __shfl_sync(0xffffffffu, d[kk], src);  // key of element k of this line
+        const uint32_t vkp = (ck & ~(M - 1)) + (uint32_t)(k + 1);    // M * (its value) + k + 1
+        const uint32_t* Sk = reinterpret_cast<const uint32_t*>(S) + k * DS + q * RPT;
+#pragma unroll
+        for (int e4 = 0; e4 < RPT; e4 += 4) {
+          const uint4 v = *reinterpret_cast<const uint4*>(Sk + e4);
+          d[e4] = min(d[e4], v.x * M + vkp);
+          d[e4 + 1] = min(d[e4 + 1], v.y * M + vkp);
+          d[e4 + 2] = min(d[e4 + 2], v.z * M + vkp);
+          d[e4 + 3] = min(d[e4 + 3], v.w * M + vkp);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) {
+      const uint32_t sl = d[e] & (M - 1);
+      d[e] /= M;
+      if (sl != 0) p[e] = kb + (int)sl - 1;
+    }
+    keyed = true;
   }
   if (!keyed) for (int qo = 0; qo < L::TPL; ++qo) {
     const int src = qo * L::LPW + jj;
