@@ -62,8 +62,10 @@ enum {
 
 /*
  * Per-call options. Zero-initialise and set what you need.
- *   bs:       block size BS (Section 4.1). 0 = the library default for n
- *             (apsp_default_bs); else 32, 64 or 128.
+ *   bs:       block size BS (Section 4.1). 0 = the library default: on the
+ *             fp32 path apsp_default_bs(n), on the 16-bit path 128 for
+ *             n > 16384 and apsp_default_bs(n) otherwise (apsp_run_info.bs_used
+ *             reports it); else 32, 64 or 128.
  *   dtype:    APSP_DTYPE_*. U16X2 is eligible only when every finite weight is
  *             an integer and max_w * (n - 1) < 65535, so that every path length
  *             fits in 16 bits; it gives bit-identical D and P to F32.
@@ -114,7 +116,7 @@ typedef struct {
  */
 apsp_status apsp_device_status(int clear);
 
-/* Library default block size for order n (deterministic in n). */
+/* Library default block size of the fp32 path for order n (deterministic in n). */
 int apsp_default_bs(int n);
 
 /*

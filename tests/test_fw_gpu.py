@@ -83,7 +83,7 @@ def test_config_n512_dense_int():
         _expect_exact(W, D, P, bs)
 
 
-@pytest.mark.parametrize("n,hi,bs", [(130, 2, 32), (300, 100, 64), (520, 20, 32), (256, 255, 128)])
+@pytest.mark.parametrize("n,hi,bs", [(130, 2, 32), (300, 100, 64), (520, 20, 32), (256, 255, 128), (389, 60, 128)])
 def test_u16_path_bit_exact(n, hi, bs):
     W = inputs.dense_digraph(n, seed=3000 + n, lo=1, hi=hi, density=0.5)
     assert hi * (n - 1) < 65535
@@ -267,7 +267,7 @@ def test_deterministic_repeats():
 # ---------------------------------------------------------------- full benchmark sizes (sampled)
 
 def _sampled_check(n, seed, lo, hi, density, kind, bs, n_src=6, n_pairs=20000, dtype=apsp.DTYPE_AUTO,
-                   expect_dtype=None):
+                   expect_dtype=None, expect_bs=None):
     Wd = inputs.dense_digraph(n, seed, lo, hi, density=density, kind=kind, device=DEV)
     D = torch.empty_like(Wd)
     P = torch.empty((n, n), dtype=torch.int32, device=DEV)
@@ -275,6 +275,8 @@ def _sampled_check(n, seed, lo, hi, density, kind, bs, n_src=6, n_pairs=20000, d
     torch.cuda.synchronize()
     if expect_dtype is not None:
         assert info.dtype_used == expect_dtype
+    if expect_bs is not None:
+        assert info.bs_used == expect_bs
     W = Wd.cpu().numpy()
     del Wd
     Dh = D.cpu().numpy()
@@ -315,6 +317,12 @@ def test_full_n32768_real():
 @pytest.mark.slow
 def test_full_n32768_u16():
     _sampled_check(32768, 5, 1, 2, 1.0, "int", bs=64, n_src=4, expect_dtype=apsp.DTYPE_U16X2)
+
+
+@pytest.mark.slow
+def test_full_n32768_u16_default_block_size():
+    # the benchmark's 16-bit run: library default block size (128 on this path above n = 16384)
+    _sampled_check(32768, 5, 1, 2, 1.0, "int", bs=0, n_src=4, expect_dtype=apsp.DTYPE_U16X2, expect_bs=128)
 
 
 def test_autotuner_returns_a_valid_block_size():
