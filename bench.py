@@ -306,7 +306,7 @@ def run_gpu(args, rank: int, world: int):
             "peak": round(ALU_PEAK_F32_TFLOPS, 2), "unit": "TFLOP/s",
             "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
             "traffic": _traffic_from_profile(n, args.bs, args.kind),
-            "kernel": f"fw_phase3_f32_kernel<{args.bs}, {'true' if args.kind == 'real' else 'false'}>",
+            "kernel": f"fw_phase3_f32_real_kernel<{args.bs}>" if args.kind == "real" else f"fw_phase3_f32_kernel<{args.bs}>",
             "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
             "phase_ms_per_step": [round(x / ph_steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // ph_steps for x in ph_launch],

@@ -115,7 +115,7 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   constexpr size_t sm1 = phase1_smem_bytes<T, BS>();
   constexpr size_t sm2 = phase2_smem_bytes<T, BS>();
   constexpr size_t sm3 = std::is_same<T, F32T>::value ? minplus_f32_smem_bytes<BS>() : minplus_u16_smem_bytes<BS>();
-  constexpr size_t sm3r = minplus_f32_smem_bytes<BS, true>();
+  constexpr size_t sm3r = minplus_f32_real_smem_bytes<BS>();
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -125,8 +125,8 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
     if (e1 == cudaSuccess) e1 = e0;
     cudaError_t e2, e3 = cudaSuccess;
     if constexpr (std::is_same<T, F32T>::value) {
-      e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-      e3 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3r);
+      e2 = cudaFuncSetAttribute(fw_phase3_f32_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+      e3 = cudaFuncSetAttribute(fw_phase3_f32_real_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3r);
     } else {
       e2 = cudaFuncSetAttribute(fw_phase3_u16_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
     }
@@ -154,17 +154,24 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
                        static_cast<const reg_t*>(pk), wait_ns, (int)test_timeout, graph_int));
       tm.mark(1);
       if constexpr (std::is_same<T, F32T>::value) {
-        keep(launch_dependent(fw_pack_panels_f32_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const float*>(D), ld, nT, r,
-                         static_cast<const RoundMax*>(rm), graph_int, Apk, Bpk));
-        ++tm.other;
-        if (graph_int)
-          keep(launch_dependent(fw_phase3_f32_kernel<BS, false>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
-                           static_cast<const RoundMax*>(rm), graph_int, static_cast<const float*>(Apk),
-                           static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
-        else
-          keep(launch_dependent(fw_phase3_f32_kernel<BS, true>, nT * nT, 256, sm3r, s, D, P, ld, nT, r,
-                           static_cast<const RoundMax*>(rm), 0, static_cast<const float*>(Apk),
-                           static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
+        if (graph_int) {
+          keep(launch_dependent(fw_pack_panels_f32_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const float*>(D), ld,
+                                nT, r, static_cast<const RoundMax*>(rm), graph_int, Apk, Bpk));
+          ++tm.other;
+          keep(launch_dependent(fw_phase3_f32_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
+                                static_cast<const RoundMax*>(rm), graph_int, static_cast<const float*>(Apk),
+                                static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
+        } else {
+          // real-valued weights: B slices 64 columns wide, tiles of 128 x 64
+          const int nTc = nT * (kTile / kRealCols);
+          keep(launch_dependent(fw_pack_panels_f32_kernel<BS, kRealCols>, nT + nTc, 256, 0, s,
+                                static_cast<const float*>(D), ld, nT, r, static_cast<const RoundMax*>(rm), 0, Apk,
+                                Bpk));
+          ++tm.other;
+          keep(launch_dependent(fw_phase3_f32_real_kernel<BS>, nT * nTc, 256, sm3r, s, D, P, ld, nT, r,
+                                static_cast<const float*>(Apk), static_cast<const float*>(Bpk), kStaggerCycles, sms,
+                                wait_ns, (int)test_timeout));
+        }
       } else {
         uint32_t* Apk16 = reinterpret_cast<uint32_t*>(pan);
         uint32_t* Bpk16 = Apk16 + (size_t)nT * u16_slice_a_words<BS>();
@@ -211,7 +218,10 @@ constexpr size_t kRoundMaxOffset = 64;  // RoundMax inside the 256-byte head
 static size_t packed_panel_bytes(int n_pad, int bs, int dtype) {
   const size_t nT = (size_t)(n_pad / kTile);
   if (dtype == APSP_DTYPE_U16X2) return nT * (size_t)bs * (kSstA16 + kSstB16) * sizeof(uint32_t);
-  return 2 * nT * (size_t)(bs / 2) * kS2 * sizeof(float);
+  // A slices plus B slices 128 columns wide (integer weights) or 64 wide (real weights)
+  const size_t a = nT * (size_t)(bs / 2) * kS2;
+  const size_t b = std::max(nT * (size_t)(bs / 2) * kS2, 2 * nT * (size_t)(bs / 2) * kRealSB);
+  return (a + b) * sizeof(float);
 }
 static void layout(Plan& pl, bool p_in_place) {
   const size_t np2 = (size_t)pl.n_pad * pl.n_pad;

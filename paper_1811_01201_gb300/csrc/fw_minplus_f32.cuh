@@ -20,14 +20,13 @@
 //    and, among equal values, the smallest k -- while the old D (slot 0) wins
 //    ties, as the strict '<' requires. Slot 0 in the result means unchanged,
 //    so neither the old tile nor a search is needed: P comes for free.
-//  * otherwise (real-valued weights, large distances): improved elements are
-//    found by comparing with the old D. On real-valued graphs the warp lists
-//    the improved elements in shared memory and each lane scans one listed
-//    element's candidates with k ascending up to the first whose sum equals
-//    D'. On integer graphs (whose rounds without keys are rare), where many
-//    improved every lane re-scans its own elements with k descending, else
-//    the warp re-evaluates one improved element at a time, one k per lane.
-//    All use bit-identical additions, so equality is exact.
+//  * rounds of integer graphs beyond that bound (rare): improved elements are
+//    found by comparing with the old D; where many improved every lane
+//    re-scans its own elements with k descending, else the warp re-evaluates
+//    one improved element at a time, one k per lane. Real-valued graphs run
+//    fw_phase3_f32_real_kernel (end of this file), which tags each element
+//    with the group of k pairs of its last improvement. All searches use
+//    bit-identical additions, so equality is exact.
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads, 8 x 8 elements per
 // thread in registers (rows ty*4+{0..3}, 64+ty*4+{0..3}; columns likewise
@@ -64,11 +63,10 @@ constexpr int kS2 = 2 * kTile + 8;  // floats per k-pair row (padded)
 
 // Per-warp list of improved elements for the P search of real-valued graphs.
 constexpr int kQueuePerWarp = 384;
-constexpr int kQueueFlush = kQueuePerWarp - 256;
 
-template <int BS, bool REAL = false>
+template <int BS>
 constexpr size_t minplus_f32_smem_bytes() {
-  return sizeof(float) * (size_t)BS * kS2 + (REAL ? sizeof(int2) * 8 * kQueuePerWarp : 0);
+  return sizeof(float) * (size_t)BS * kS2;
 }
 
 __device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
@@ -95,15 +93,12 @@ __device__ __forceinline__ float floor_pos(float v) {
   return __fsub_rn(__fadd_rd(v, 8388608.f), 8388608.f);
 }
 
-// REAL: the graph has non-integer weights, so keys never apply and every
-// improved element goes through a per-warp list. Integer graphs keep the short
-// search code (their rounds without keys are rare), which leaves the key
-// path's registers alone.
-template <int BS, bool REAL>
+// Integer-valued graphs (graphs with other weights use
+// fw_phase3_f32_real_kernel below).
+template <int BS>
 __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __restrict__ P, size_t ld, int kb,
-                                          int r0, int c0, bool keyed_in, float* As, float* Bs, int2* queue,
-                                          uint64_t* bar, unsigned long long wait_ns) {
-  const bool keyed = REAL ? false : keyed_in;
+                                          int r0, int c0, bool keyed, float* As, float* Bs, uint64_t* bar,
+                                          unsigned long long wait_ns) {
   constexpr float M = KeyParams<BS>::M;
   const float INF = f32_inf();
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -183,79 +178,6 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
           for (int e = 0; e < 4; ++e)
             if (sl[e] != 0) P[(size_t)gi * ld + gj + e] = kb + sl[e] - 1;
         }
-      }
-    }
-    return;
-  }
-  if constexpr (REAL) {
-    // Row by row: compare with the old D, write the improved values, and list
-    // the improved elements (row << 8 | column, new value) in the warp's
-    // shared-memory queue. Once the queue holds kQueueFlush or more (a row adds
-    // at most 256), each lane takes listed elements and scans their candidates
-    // with k ascending up to the first whose sum equals the new value.
-    int2* wq = queue + warp * kQueuePerWarp;
-    const unsigned lt = (1u << lane) - 1u;
-    int cnt = 0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int li = mp_row(ty, a);
-      const int gi = r0 + li;
-      const bool band_r = (gi >= kb) && (gi < kb + BS);
-      unsigned rimp = 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int gj = c0 + mp_col(tx, 4 * h);
-        const bool band_c = (gj >= kb) && (gj < kb + BS);
-        if (band_r || band_c) continue;
-        float* dp = D + (size_t)gi * ld + gj;
-        const float4 o4 = *reinterpret_cast<const float4*>(dp);
-        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-        float nv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool im = d[a][4 * h + e] < old[e];
-          nv[e] = im ? d[a][4 * h + e] : old[e];
-          if (im) rimp |= 1u << (4 * h + e);
-        }
-        if (rimp >> (4 * h)) *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const bool bit = (rimp >> c) & 1;
-        const unsigned bal = __ballot_sync(0xffffffffu, bit);
-        if (bit) wq[cnt + __popc(bal & lt)] = make_int2((li << 8) | mp_col(tx, c), __float_as_int(d[a][c]));
-        cnt += __popc(bal);
-      }
-      if (cnt >= kQueueFlush || (a == 7 && cnt > 0)) {
-        __syncwarp();
-        for (int e = lane; e < cnt; e += 32) {
-          const int2 ent = wq[e];
-          const int qi = ent.x >> 8, qj = ent.x & 255;
-          const float dn = __int_as_float(ent.y);
-          // eight k-pairs (16 candidates) per step, their loads in flight together
-          int kstar = BS;
-#pragma unroll 1
-          for (int kp0 = 0; kp0 < BS / 2; kp0 += 8) {
-            float2 c2[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              c2[u] = fadd2_rn(*reinterpret_cast<const float2*>(As + (kp0 + u) * kS2 + 2 * qi),
-                               *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kS2 + 2 * qj));
-            int m = BS;
-#pragma unroll
-            for (int u = 7; u >= 0; --u) {
-              if (c2[u].y == dn) m = 2 * (kp0 + u) + 1;
-              if (c2[u].x == dn) m = 2 * (kp0 + u);
-            }
-            if (m < BS) {
-              kstar = m;
-              break;
-            }
-          }
-          P[(size_t)(r0 + qi) * ld + c0 + qj] = kb + kstar;
-        }
-        __syncwarp();
-        cnt = 0;
       }
     }
     return;
@@ -369,8 +291,16 @@ __device__ __forceinline__ bool round_keyed(const RoundMax* rm, int graph_int) {
          __int_as_float((int)rm->a_bits) + __int_as_float((int)rm->b_bits) <= KeyParams<BS>::bound;
 }
 
-// CTAs 0 .. nT-1 pack the A slices (tile rows), nT .. 2nT-1 the B slices (tile columns).
-template <int BS>
+// Floats per k-pair row of a B slice WB columns wide (128 for the integer
+// kernel, 64 for the real-weight kernel), padded like kS2.
+template <int WB>
+__host__ __device__ constexpr int b_slice_stride() {
+  return 2 * WB + 8;
+}
+
+// CTAs 0 .. nT-1 pack the A slices (tile rows), the next n_pad/WB CTAs the B
+// slices (column tiles WB wide).
+template <int BS, int WB = kTile>
 __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __restrict__ D, size_t ld, int nT, int r,
                                                                  const RoundMax* __restrict__ rm, int graph_int,
                                                                  float* __restrict__ Apk, float* __restrict__ Bpk) {
@@ -398,15 +328,16 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
     }
   } else {
     // rows 2kp and 2kp+1 of one column quad -> two interleaved 128-bit stores
-    const int tc = blockIdx.x - nT, c0 = tc * kTile;
-    float* Bs = Bpk + panel_slice_floats<BS>() * tc;
+    constexpr int QW = WB / 4, SB = b_slice_stride<WB>();
+    const int tc = blockIdx.x - nT, c0 = tc * WB;
+    float* Bs = Bpk + (size_t)(BS / 2) * SB * tc;
 #pragma unroll
-    for (int m = 0; m < BS / 16; ++m) {
-      const int idx = tid + 256 * m, kp = idx >> 5, q = idx & 31;
+    for (int m = 0; m < (BS / 2) * QW / 256; ++m) {
+      const int idx = tid + 256 * m, kp = idx / QW, q = idx % QW;
       const float4 x = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp) * ld + c0 + q * 4);
       const float4 y = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp + 1) * ld + c0 + q * 4);
-      *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
-      *reinterpret_cast<float4*>(Bs + kp * kS2 + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
+      *reinterpret_cast<float4*>(Bs + kp * SB + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
+      *reinterpret_cast<float4*>(Bs + kp * SB + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
     }
   }
 }
@@ -424,7 +355,7 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
 //              wait expires (the timeout path, with no copy in flight)
 // A thread issues two bulk copies (the A and B slices of this tile) before the
 // CTA loads its tile, so the copies overlap the tile load.
-template <int BS, bool REAL>
+template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
                                                                size_t ld, int nT, int r, const RoundMax* __restrict__ rm,
                                                                int graph_int, const float* __restrict__ Apk,
@@ -438,7 +369,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
   const int r0 = tr * kTile, c0 = tc * kTile;
   // Tiles entirely inside row band r or column band r belong to phases 1-2.
   if ((r0 >= kb && r0 + kTile <= kb + BS) || (c0 >= kb && c0 + kTile <= kb + BS)) return;
-  const bool keyed = !REAL && round_keyed<BS>(rm, graph_int);
+  const bool keyed = round_keyed<BS>(rm, graph_int);
   if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
   float* As = sm;
   float* Bs = sm + panel_slice_floats<BS>();
@@ -452,7 +383,165 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
       bulk_copy_g2s(Bs, Bpk + panel_slice_floats<BS>() * tc, slice_bytes, &bar);
     }
   }
-  tile_body<BS, REAL>(D, P, ld, kb, r0, c0, keyed, As, Bs, reinterpret_cast<int2*>(sm + BS * kS2), &bar, wait_ns);
+  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, As, Bs, &bar, wait_ns);
+}
+
+// ---------------------------------------------------------------- real-valued graphs
+//
+// Phase 3 for graphs with non-integer weights (no keys). One CTA of 256
+// threads per 128 x 64 tile, 8 x 4 elements per thread (rows as in the integer
+// kernel, four consecutive columns). The BS intermediates run in groups of
+// eight k pairs; at the end of each group every element compares itself with
+// its value at the group's start and, if it fell, records the group (a 4-bit
+// tag; the first group's start is the old D). The tags name every improved
+// element and the group holding its last strict improvement, which contains
+// the first k attaining its final value (an earlier group cannot reach that
+// value, or the later group could not have fallen to it). So the old tile is
+// never re-read, and each improved element is searched over 16 candidates only:
+// the warp lists them in shared memory and each lane takes listed elements.
+// The A slices are the integer kernel's; the B slices are packed 64 columns
+// wide (fw_pack_panels_f32_kernel<BS, 64>).
+constexpr int kRealCols = 64;
+constexpr int kRealSB = 2 * kRealCols + 8;      // floats per k-pair row of a B slice
+constexpr int kRealQueueFlush = kQueuePerWarp - 128;  // a row adds at most 32 x 4 entries
+
+template <int BS>
+__host__ __device__ constexpr size_t real_b_slice_floats() {
+  return (size_t)(BS / 2) * kRealSB;
+}
+
+template <int BS>
+constexpr size_t minplus_f32_real_smem_bytes() {
+  return sizeof(float) * (panel_slice_floats<BS>() + real_b_slice_floats<BS>()) + sizeof(int2) * 8 * kQueuePerWarp;
+}
+
+template <int BS>
+__global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __restrict__ D, int32_t* __restrict__ P,
+                                                                    size_t ld, int nT, int r,
+                                                                    const float* __restrict__ Apk,
+                                                                    const float* __restrict__ Bpk, int stagger,
+                                                                    int sms, unsigned long long wait_ns, int no_copy) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ uint64_t bar;
+  pdl_prologue();
+  constexpr int NG = BS / 16;  // groups of eight k pairs
+  const int kb = r * BS;
+  const int nTc = nT * (kTile / kRealCols);
+  const int tr = blockIdx.x / nTc, tc = blockIdx.x - tr * nTc;
+  const int r0 = tr * kTile, c0 = tc * kRealCols;
+  if ((r0 >= kb && r0 + kTile <= kb + BS) || (c0 >= kb && c0 + kRealCols <= kb + BS)) return;
+  if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) spin_cycles(stagger);
+  float* As = sm;
+  float* Bs = sm + panel_slice_floats<BS>();
+  int2* queue = reinterpret_cast<int2*>(Bs + real_b_slice_floats<BS>());
+  constexpr unsigned a_bytes = (unsigned)(panel_slice_floats<BS>() * sizeof(float));
+  constexpr unsigned b_bytes = (unsigned)(real_b_slice_floats<BS>() * sizeof(float));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar, a_bytes + b_bytes);
+    if (!no_copy) {
+      bulk_copy_g2s(As, Apk + panel_slice_floats<BS>() * tr, a_bytes, &bar);
+      bulk_copy_g2s(Bs, Bpk + real_b_slice_floats<BS>() * tc, b_bytes, &bar);
+    }
+  }
+  float d[8][4], ds[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + mp_row(ty, a)) * ld + c0 + tx * 4);
+    d[a][0] = v.x; d[a][1] = v.y; d[a][2] = v.z; d[a][3] = v.w;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ds[a][c] = d[a][c];
+  }
+  if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
+    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    mbar_wait_phase0(&bar, wait_ns);  // copies still in flight land before the CTA exits
+    return;
+  }
+  uint32_t tag[4] = {0u, 0u, 0u, 0u};  // element e = a*4 + c: bits 4*(e&7) of tag[e>>3]
+  const float* Ap = As + ty * 8;
+  const float* Bp = Bs + tx * 8;
+#pragma unroll 1
+  for (int g = 0; g < NG; ++g) {
+#pragma unroll 1
+    for (int u = 0; u < 8; ++u) {
+      const int kp = g * 8 + u;
+      const float4 a0 = *reinterpret_cast<const float4*>(Ap + kp * kS2);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
+      const float4 a2 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 128);
+      const float4 a3 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 132);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bp + kp * kRealSB);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bp + kp * kRealSB + 4);
+      const float2 av[8] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}, {a1.z, a1.w},
+                            {a2.x, a2.y}, {a2.z, a2.w}, {a3.x, a3.y}, {a3.z, a3.w}};
+      const float2 bv[4] = {{b0.x, b0.y}, {b0.z, b0.w}, {b1.x, b1.y}, {b1.z, b1.w}};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 sv = fadd2_rn(av[a], bv[c]);
+          d[a][c] = fminf(fminf(d[a][c], sv.x), sv.y);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int e = a * 4 + c, sh = 4 * (e & 7);
+        if (d[a][c] < ds[a][c]) tag[e >> 3] = (tag[e >> 3] & ~(0xFu << sh)) | ((uint32_t)(g + 1) << sh);
+        ds[a][c] = d[a][c];
+      }
+  }
+  // Write back improved rows of four; list improved elements (group, row, column, value).
+  int2* wq = queue + warp * kQueuePerWarp;
+  const unsigned lt = (1u << lane) - 1u;
+  const int gj = c0 + tx * 4;
+  const bool band_c = (gj >= kb) && (gj < kb + BS);
+  int cnt = 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int li = mp_row(ty, a);
+    const int gi = r0 + li;
+    const bool band = band_c || ((gi >= kb) && (gi < kb + BS));
+    const uint32_t row_tags = (tag[a >> 1] >> (16 * (a & 1))) & 0xFFFFu;  // elements a*4 .. a*4+3
+    if (!band && row_tags != 0)
+      *reinterpret_cast<float4*>(D + (size_t)gi * ld + gj) = make_float4(d[a][0], d[a][1], d[a][2], d[a][3]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t gt = (row_tags >> (4 * c)) & 0xFu;
+      const bool bit = !band && gt != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, bit);
+      if (bit)
+        wq[cnt + __popc(bal & lt)] = make_int2((int)(gt << 16) | (li << 8) | (tx * 4 + c), __float_as_int(d[a][c]));
+      cnt += __popc(bal);
+    }
+    if (cnt >= kRealQueueFlush || (a == 7 && cnt > 0)) {
+      __syncwarp();
+#pragma unroll 1
+      for (int e = lane; e < cnt; e += 32) {
+        const int2 ent = wq[e];
+        const int kp0 = ((ent.x >> 16) - 1) * 8;
+        const int qi = (ent.x >> 8) & 255, qj = ent.x & 255;
+        const float dn = __int_as_float(ent.y);
+        float2 c2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          c2[u] = fadd2_rn(*reinterpret_cast<const float2*>(As + (kp0 + u) * kS2 + 2 * qi),
+                           *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kRealSB + 2 * qj));
+        int kstar = BS;
+#pragma unroll
+        for (int u = 7; u >= 0; --u) {
+          if (c2[u].y == dn) kstar = 2 * (kp0 + u) + 1;
+          if (c2[u].x == dn) kstar = 2 * (kp0 + u);
+        }
+        P[(size_t)(r0 + qi) * ld + c0 + qj] = kb + kstar;
+      }
+      __syncwarp();
+      cnt = 0;
+    }
+  }
 }
 
 }  // namespace apsp
