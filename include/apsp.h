@@ -136,7 +136,7 @@ const char* apsp_status_str(apsp_status s);
 /*
  * Bytes of device workspace apsp_fw_ex needs for (n, opt): always at least
  * 256 (the input scan's counters) plus the round's packed panel slices
- * (ceil(n/128) * bs * 1056 bytes on the fp32 path, * 800 on the 16-bit path;
+ * (ceil(n/128) * bs * 1072 bytes on the fp32 path, * 800 on the 16-bit path;
  * bs = opt->bs, or apsp_default_bs(n) when it is 0) and the packed diagonal
  * block (8 * bs * (bs + 4) bytes); n*n-sized working
  * matrices are added when n is not a multiple of 128 or the 16-bit path may

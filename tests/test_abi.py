@@ -50,6 +50,30 @@ def test_host_only_helpers():
     assert apsp.apsp_fw_workspace_size(0) == 0
 
 
+def test_workspace_size_formula():
+    # documented in include/apsp.h: a 256-byte head, the round's packed panel slices
+    # (fp32: ceil(n/128) * bs * 1072 bytes; 16-bit: * 800) and the packed diagonal block
+    # (8 * bs * (bs + 4) bytes), each rounded up to 256 bytes; n*n working matrices only
+    # when n is not a multiple of 128 (fp32) or for the 16-bit path
+    def up(x):
+        return (x + 255) // 256 * 256
+    for n, bs in [(128, 32), (1024, 64), (32768, 64), (65536, 64), (4096, 128)]:
+        nt = n // 128
+        want = 256 + up(nt * bs * 1072) + up(8 * bs * (bs + 4))
+        assert apsp.apsp_fw_workspace_size(n, bs=bs, dtype=apsp.DTYPE_F32) == want, (n, bs)
+    n, bs = 4096, 64  # 16-bit: D16 working matrix, P in place
+    want16 = 256 + up(2 * n * n) + up((n // 128) * bs * 800) + up(8 * bs * (bs + 4))
+    f32 = 256 + up((n // 128) * bs * 1072) + up(8 * bs * (bs + 4))
+    assert apsp.apsp_fw_workspace_size(n, bs=bs) == max(want16, f32)
+    # default block size: 64 on the fp32 path above n = 512, 128 on the 16-bit path above 16384
+    assert apsp.apsp_fw_workspace_size(40000 // 128 * 128, dtype=apsp.DTYPE_F32) == \
+        apsp.apsp_fw_workspace_size(40000 // 128 * 128, bs=64, dtype=apsp.DTYPE_F32)
+    big = 20480
+    assert apsp.apsp_fw_workspace_size(big) == max(
+        apsp.apsp_fw_workspace_size(big, bs=64, dtype=apsp.DTYPE_F32),
+        256 + up(2 * big * big) + up((big // 128) * 128 * 800) + up(8 * 128 * 132))
+
+
 def test_path_helper_matches_oracle_walk():
     import oracle
     from paper_1811_01201_gb300 import inputs
