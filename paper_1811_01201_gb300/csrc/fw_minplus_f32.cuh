@@ -403,6 +403,9 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
 // wide (fw_pack_panels_f32_kernel<BS, 64>).
 constexpr int kRealCols = 64;
 constexpr int kRealSB = 2 * kRealCols + 8;      // floats per k-pair row of a B slice
+// k pairs per tagged group: 16 measured slower (n = 8192: 17.3 vs 19.4 TFLOPS;
+// n = 32768: 24.3 vs 25.0), as the searches double while the bookkeeping halves.
+constexpr int kRealGroup = 8;
 constexpr int kRealQueueFlush = kQueuePerWarp - 128;  // a row adds at most 32 x 4 entries
 
 template <int BS>
@@ -424,7 +427,8 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
   extern __shared__ __align__(16) float sm[];
   __shared__ uint64_t bar;
   pdl_prologue();
-  constexpr int NG = BS / 16;  // groups of eight k pairs
+  constexpr int NG = BS / (2 * kRealGroup);  // groups of kRealGroup k pairs (tags 1..NG fit in 4 bits)
+  static_assert(NG >= 1 && NG <= 15, "group tags need 4 bits");
   const int kb = r * BS;
   const int nTc = nT * (kTile / kRealCols);
   const int tr = blockIdx.x / nTc, tc = blockIdx.x - tr * nTc;
@@ -466,8 +470,8 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
 #pragma unroll 1
   for (int g = 0; g < NG; ++g) {
 #pragma unroll 1
-    for (int u = 0; u < 8; ++u) {
-      const int kp = g * 8 + u;
+    for (int u = 0; u < kRealGroup; ++u) {
+      const int kp = g * kRealGroup + u;
       const float4 a0 = *reinterpret_cast<const float4*>(Ap + kp * kS2);
       const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
       const float4 a2 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 128);
@@ -522,17 +526,17 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
 #pragma unroll 1
       for (int e = lane; e < cnt; e += 32) {
         const int2 ent = wq[e];
-        const int kp0 = ((ent.x >> 16) - 1) * 8;
+        const int kp0 = ((ent.x >> 16) - 1) * kRealGroup;
         const int qi = (ent.x >> 8) & 255, qj = ent.x & 255;
         const float dn = __int_as_float(ent.y);
-        float2 c2[8];
+        float2 c2[kRealGroup];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < kRealGroup; ++u)
           c2[u] = fadd2_rn(*reinterpret_cast<const float2*>(As + (kp0 + u) * kS2 + 2 * qi),
                            *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kRealSB + 2 * qj));
         int kstar = BS;
 #pragma unroll
-        for (int u = 7; u >= 0; --u) {
+        for (int u = kRealGroup - 1; u >= 0; --u) {
           if (c2[u].y == dn) kstar = 2 * (kp0 + u) + 1;
           if (c2[u].x == dn) kstar = 2 * (kp0 + u);
         }
