@@ -3,9 +3,11 @@
 // Per call: validate, pick the arithmetic (fp32, or exact 16-bit when every
 // path length fits), lay D/P out in a working layout whose order is a multiple
 // of 128, then run R = n_pad/BS block rounds (Section 4.1 of arXiv 1811.01201),
-// each as three stream-ordered launches: phase 1 (diagonal block), phase 2
-// (its row and column blocks), phase 3 (all remaining blocks). Kernel
-// boundaries are the barriers between the phases.
+// each as four stream-ordered launches: phase 1 (diagonal block), phase 2 (its
+// row and column blocks), the panel pack, phase 3 (all remaining blocks).
+// Kernel boundaries are the barriers between the phases; the kernels are
+// launched as programmatic dependents, so each is scheduled while its
+// predecessor runs and waits on the device for it to finish.
 #include <cuda_runtime.h>
 
 #include <algorithm>

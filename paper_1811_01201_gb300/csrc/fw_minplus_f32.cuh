@@ -82,11 +82,8 @@ __device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
 
 __device__ __forceinline__ float pan(const float* S, int k, int x) { return S[(k >> 1) * kS2 + 2 * x + (k & 1)]; }
 
-
 __device__ __forceinline__ int mp_row(int ty, int a) { return (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
 __device__ __forceinline__ int mp_col(int tx, int c) { return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
-
-__device__ __forceinline__ bool is_int_or_inf(float v) { return !(v < f32_inf()) || v == floorf(v); }
 
 __device__ __forceinline__ float floor_pos(float v) {
   // floor for 0 <= v < 2^23 on the FMA pipe: round-down add of 2^23, then subtract
