@@ -302,7 +302,7 @@ apsp_status apsp_serve_destroy(apsp_server* s);
  *   Limit: apsp_fw_workspace_size(n, opt) must not exceed
  *     APSP_NOALLOC_SCRATCH_BYTES, else APSP_ENOMEM and nothing is enqueued.
  *     With dtype F32 that allows any n that is a multiple of 128 (up to
- *     63360 with bs = 128, whose packed panel slices are larger) and any
+ *     62464 with bs = 128, whose packed panel slices are larger) and any
  *     n <= 2816 otherwise; AUTO / U16X2 allow n <= 2816, or n <= 5632 (5504
  *     with bs = 128) when n is a multiple of 128 (room for the 16-bit
  *     working matrix).
