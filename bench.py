@@ -278,13 +278,17 @@ def run_gpu(args, rank: int, world: int):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)
+        marks = []
         for _ in range(args.steps):
             info = step()
             launches += info.launches
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(s)
         e1.record(s)
         torch.cuda.synchronize()
         barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    per_step = [e0.elapsed_time(marks[0])] + [marks[i - 1].elapsed_time(marks[i]) for i in range(1, len(marks))]
     # Per-phase device time from separate steps that record an event after every launch (the
     # events keep each launch from overlapping its predecessor, so these steps run apart from
     # the timed ones).
@@ -328,6 +332,8 @@ def run_gpu(args, rank: int, world: int):
 
     line = {"metric": "APSP GFLOPS (2n^3/s)", "value": round(value, 2), "unit": "GFLOPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+            "ms_per_step_min_median_max": [round(min(per_step), 3), round(statistics.median(per_step), 3),
+                                           round(max(per_step), 3)],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(args) | {"parallelism": f"replicas x{world}"},
             "gpu_launches": launches, "roofline": roof, "clocks": clocks}

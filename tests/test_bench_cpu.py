@@ -87,3 +87,20 @@ def test_profile_traffic_parser(tmp_path, monkeypatch):
     assert bench._traffic_from_profile(32768, 128) is None          # other block size
     src.write_text("// changed kernel\n")
     assert bench._traffic_from_profile(32768, 64, "real") is None   # stale capture
+
+
+def test_clock_sampler_summary_reasons():
+    # rows as nvidia-smi prints them (noheader, nounits): index, sm MHz, max MHz, power,
+    # active mask, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    sys.path.insert(0, ROOT)
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.rows = [["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["0", "1950", "2070", "1400.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+               ["0", "2070", "2070", "1200.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["0", "[N/A]", "2070"]]  # a malformed sample is skipped
+    sm = cs.summary()
+    assert sm["sm_mhz"] == 2070.0 and sm["sm_max_mhz"] == 2070.0 and sm["samples"] == 3
+    assert sm["reasons"] == ["sw_power_cap"]
+    cs.rows.append(["0", "1200", "2070", "600.0", "0x40", "Not Active", "Active", "Not Active", "Not Active"])
+    assert "hw_thermal_slowdown" in cs.summary()["reasons"]
