@@ -325,6 +325,52 @@ def test_full_n32768_u16_default_block_size():
     _sampled_check(32768, 5, 1, 2, 1.0, "int", bs=0, n_src=4, expect_dtype=apsp.DTYPE_U16X2, expect_bs=128)
 
 
+def _host_available_bytes() -> int:
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    return 0
+
+
+@pytest.mark.slow
+def test_max_n65536_int_in_place():
+    # The largest n the library accepts: element offsets pass 2^31 and 2^32. Solved in place
+    # (W aliases D) to keep the device at 32 GiB; the host keeps W only (16 GiB). Sampled rows
+    # of D against Dijkstra, the optimality condition on those rows, and every P entry of
+    # those rows: -1 only where D is the direct edge, else an intermediate k with
+    # D[s][j] == D[s][k] + D[k][j] (exact for integer weights).
+    n, seed = 65536, 6
+    if _host_available_bytes() < (n * n * 4) + (32 << 30):
+        pytest.skip("not enough free host memory for a 16 GiB copy of W")
+    if torch.cuda.mem_get_info()[0] < 2 * n * n * 4 + (8 << 30):
+        pytest.skip("not enough free device memory for D and P at n=65536")
+    D = inputs.dense_digraph(n, seed, 1, 1000, device=DEV)
+    W = D.cpu().numpy()
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    info = apsp.apsp_fw_ex(D, D, P)
+    torch.cuda.synchronize()
+    assert info.dtype_used == apsp.DTYPE_F32 and info.bs_used == 64
+    rng = np.random.default_rng(seed)
+    cols = torch.arange(n, device=DEV)
+    for s in [0, n - 1] + [int(v) for v in rng.choice(n, size=2, replace=False)]:
+        row = D[s].cpu().numpy()
+        np.testing.assert_array_equal(row.astype(np.float64), oracle.dijkstra(W, s))
+        assert oracle.check_bellman_row(W, row) == 0
+        k = P[s].long()
+        direct = k < 0
+        via = D[k.clamp(min=0), cols].cpu().numpy()
+        kh, dh = k.cpu().numpy(), direct.cpu().numpy()
+        w = W[s].copy()
+        w[s] = 0.0
+        np.testing.assert_array_equal(row[dh], w[dh])
+        j = np.nonzero(~dh)[0]
+        assert ((kh[j] != s) & (kh[j] != j) & (kh[j] < n)).all()
+        np.testing.assert_array_equal(row[j], row[kh[j]] + via[j])
+    del D, P
+    torch.cuda.empty_cache()
+
+
 def test_autotuner_returns_a_valid_block_size():
     bs, ms = apsp.apsp_autotune_bs(1024)
     assert bs in (32, 64, 128)
