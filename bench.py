@@ -39,14 +39,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Roofline denominators (unit counts x clock): 152 SMs; the FP32 min (FMNMX)
-# issues at 64 lanes/clk/SM on the ALU pipe, one per relaxation, so the fp32
-# update peak is 152 * 64 * f updates/s = 2 * 152 * 64 * f "flops"/s in the 2n^3
-# convention; the packed 16-bit path (min.u16x2: 2 mins per lane) doubles it.
+# Roofline denominators (unit counts x clock), from the issue rates that
+# csrc/probes/min_rates.cu measures on register operands: 152 SMs, one warp
+# instruction per clock per SM sub-partition (128 lanes/clk/SM). The FP32 min
+# issues at full rate, and the three-input min the compiler forms from two
+# successive mins at half rate, so one relaxation costs one min lane:
+# 128 relaxations/clk/SM. The fp32 pattern (add.rn.f32x2 + two mins per k pair)
+# also takes two issue slots per two relaxations, the same bound. The 16-bit
+# pattern (add.u16x2 + min.u16x2, two relaxations each) is issue-bound at the
+# same 128. Peak "flops"/s = 2 * 152 * 128 * f in the 2n^3 convention.
 SMS = 152
 SM_MAX_MHZ = 2070.0
-ALU_PEAK_F32_TFLOPS = 2 * SMS * 64 * SM_MAX_MHZ * 1e6 / 1e12      # 40.27
+ALU_PEAK_F32_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
+# What the fp32 instruction mix reaches with every operand in registers
+# (min_rates.cu: 106.1 relaxations/clk/SM, 8 independent chains per thread).
+PATTERN_CEILING_F32_TFLOPS = 2 * SMS * 106.1 * SM_MAX_MHZ * 1e6 / 1e12  # 66.77
 
 
 def _hbm_peak():
@@ -311,7 +319,10 @@ def run_gpu(args, rank: int, world: int):
             "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
             "traffic": _traffic_from_profile(n, args.bs, args.kind),
             "kernel": f"fw_phase3_f32_real_kernel<{args.bs}>" if args.kind == "real" else f"fw_phase3_f32_kernel<{args.bs}>",
-            "peak_source": "derived: 152 SMs x 64 FP32-min lanes/clk x 2070 MHz x 2 flop (not measured)",
+            "peak_source": "derived: 152 SMs x 128 relaxations/clk (one min lane each; min rates measured by "
+                           "csrc/probes/min_rates.cu) x 2070 MHz x 2 flop",
+            "pattern_ceiling_tflops": round(PATTERN_CEILING_F32_TFLOPS, 2),
+            "frac_of_pattern_ceiling": round(ph3_tflops / PATTERN_CEILING_F32_TFLOPS, 4) if ph3_tflops else None,
             "phase_ms_per_step": [round(x / ph_steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // ph_steps for x in ph_launch],
             "phase_steps": ph_steps}
