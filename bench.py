@@ -53,8 +53,12 @@ SM_MAX_MHZ = 2070.0
 ALU_PEAK_F32_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 # What the fp32 instruction mix reaches with every operand in registers
-# (min_rates.cu: 106.1 relaxations/clk/SM, 8 independent chains per thread).
+# (min_rates.cu: 106.1 relaxations/clk/SM, 8 independent chains per thread),
+# and what each phase-3 kernel's register tile per thread allows with no
+# memory instruction (8x8 for the integer kernel: 68.6; 8x4 for the real one: 78.7).
 PATTERN_CEILING_F32_TFLOPS = 2 * SMS * 106.1 * SM_MAX_MHZ * 1e6 / 1e12  # 66.77
+TILE_CEILING_F32_TFLOPS = {"int": 2 * SMS * 68.6 * SM_MAX_MHZ * 1e6 / 1e12,    # 43.17
+                           "real": 2 * SMS * 78.7 * SM_MAX_MHZ * 1e6 / 1e12}   # 49.53
 
 
 def _hbm_peak():
@@ -323,6 +327,8 @@ def run_gpu(args, rank: int, world: int):
                            "csrc/probes/min_rates.cu) x 2070 MHz x 2 flop",
             "pattern_ceiling_tflops": round(PATTERN_CEILING_F32_TFLOPS, 2),
             "frac_of_pattern_ceiling": round(ph3_tflops / PATTERN_CEILING_F32_TFLOPS, 4) if ph3_tflops else None,
+            "tile_ceiling_tflops": round(TILE_CEILING_F32_TFLOPS[args.kind], 2),
+            "frac_of_tile_ceiling": round(ph3_tflops / TILE_CEILING_F32_TFLOPS[args.kind], 4) if ph3_tflops else None,
             "phase_ms_per_step": [round(x / ph_steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // ph_steps for x in ph_launch],
             "phase_steps": ph_steps}

@@ -5,9 +5,10 @@
 // Standalone program, not part of the library:
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -std=c++17 -o min_rates min_rates.cu && ./min_rates
 //
-// Every case runs 8 (or 16) independent chains per thread, 256 threads x 4
-// CTAs per SM, and reports units per clock per SM at 2070 MHz (the maximum SM
-// clock; the clock is not sampled here). An empty volatile asm on an operand
+// The instruction cases run 8 (or 16) independent chains per thread; the
+// register-tile cases 16 to 64, with the occupancy their registers allow. All
+// launch 256 threads x 4 CTAs per SM and report units per clock per SM at
+// 2070 MHz (the maximum SM clock; the clock is not sampled here). An empty volatile asm on an operand
 // each step keeps the compiler from hoisting or folding; where the
 // accumulator also passes through one, two successive mins cannot be fused
 // into a three-input min.
@@ -105,6 +106,42 @@ __global__ void rate_kernel(uint32_t* out, int iters, uint32_t seed) {
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The phase-3 register tile: RA x RC accumulators per thread, each k pair
+// one add.rn.f32x2 per (a, c) and two mins, operands renewed every step (as
+// the kernel renews them from shared memory) but never loaded.
+template <int RA, int RC, int MINB>
+__global__ void __launch_bounds__(256, MINB) outer_kernel(uint32_t* out, int iters, uint32_t seed) {
+  float d[RA][RC];
+  float2 av[RA], bv[RC];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    av[a] = make_float2((float)(seed + a), (float)(2 * seed + a));
+#pragma unroll
+    for (int c = 0; c < RC; ++c) d[a][c] = 1e6f + a * RC + c + threadIdx.x;
+  }
+#pragma unroll
+  for (int c = 0; c < RC; ++c) bv[c] = make_float2((float)(3 * seed + c), (float)(5 * seed + c));
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int a = 0; a < RA; ++a) asm volatile("" : "+f"(av[a].x), "+f"(av[a].y));
+#pragma unroll
+    for (int c = 0; c < RC; ++c) asm volatile("" : "+f"(bv[c].x), "+f"(bv[c].y));
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        const float2 s = add_f32x2(av[a], bv[c]);
+        d[a][c] = fminf(fminf(d[a][c], s.x), s.y);
+      }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int c = 0; c < RC; ++c) s += __float_as_uint(d[a][c]);
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 struct Row {
   const char* name;
   void (*kernel)(uint32_t*, int, uint32_t);
@@ -134,6 +171,9 @@ int main() {
       {"add.u16x2 + min.u16x2, 8 chains", rate_kernel<kRelaxU16, 8>, 8, 2.0, "relax"},
       {"__viaddmin_s32", rate_kernel<kAddMinS32, 8>, 8, 1.0, "instr"},
       {"__viaddmin_u16x2", rate_kernel<kAddMinU16x2, 8>, 8, 1.0, "instr"},
+      {"8x8 register tile (phase-3 kernel)", outer_kernel<8, 8, 2>, 64, 2.0, "relax"},
+      {"8x4 register tile", outer_kernel<8, 4, 3>, 32, 2.0, "relax"},
+      {"4x4 register tile", outer_kernel<4, 4, 4>, 16, 2.0, "relax"},
   };
   for (const Row& r : rows) {
     float ms = 0.f;
