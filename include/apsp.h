@@ -141,8 +141,15 @@ const char* apsp_status_str(apsp_status s);
  * block (8 * bs * (bs + 4) bytes); n*n-sized working
  * matrices are added when n is not a multiple of 128 or the 16-bit path may
  * be chosen. Returns 0 on invalid arguments (apsp_fw_ex reports them).
+ * The figure assumes that D and P start on 16-byte boundaries, as every
+ * cudaMalloc and PyTorch allocation does: the solve runs in place in the
+ * caller's D and P only then. apsp_fw_workspace_size_for gives the need for
+ * the actual D and P (a misaligned one adds its padded working copy,
+ * 4 * n_pad^2 bytes). apsp_fw_ex checks a caller workspace against that
+ * need before it enqueues anything and returns APSP_ENOMEM if it is short.
  */
 size_t apsp_fw_workspace_size(int n, const apsp_options* opt);
+size_t apsp_fw_workspace_size_for(int n, const apsp_options* opt, const float* D, const int32_t* P);
 
 /*
  * All-pairs shortest paths of one graph (Section 3; blocked per Section 4.1).
@@ -271,10 +278,28 @@ apsp_status apsp_serve_create(apsp_server** out, size_t hbm_budget_bytes, int ma
 apsp_status apsp_serve_submit(apsp_server* s, const float* W, int n, uint64_t* job_id);
 
 /*
+ * apsp_serve_submit with per-job options (opt NULL = as apsp_serve_submit):
+ *   bs:    0 = the default, else 32, 64 or 128;
+ *   dtype: AUTO (the 16-bit path where eligible), F32, or U16X2 (APSP_EINVAL
+ *          for an ineligible W);
+ *   flags: 0 or APSP_FLAG_TEST_PANEL_TIMEOUT (testing only: the job's
+ *          bounded device waits expire, and its poll returns APSP_ETIMEOUT);
+ *          other flags are rejected with APSP_EINVAL;
+ *   validate: ignored (the server always checks W on the host).
+ * Graphs of order <= 512 with bs 0/32, dtype AUTO/F32 and no flag join the
+ * batched launches; every other job runs the single-graph path with its
+ * options. A job whose device waits expired fails alone: jobs running beside
+ * it are not affected.
+ */
+apsp_status apsp_serve_submit_ex(apsp_server* s, const float* W, int n, const apsp_options* opt, uint64_t* job_id);
+
+/*
  * Wait up to timeout_ms (0 = don't wait, < 0 = forever) for job_id and copy
  * its result to HOST buffers D (n*n fp32) and P (n*n int32); either may be
  * NULL. On success the job is released. Returns APSP_EBUSY / APSP_ETIMEOUT
- * while it is not ready, APSP_ENOTFOUND for an unknown id. bs_used (may be
+ * while it is not ready, APSP_ENOTFOUND for an unknown id. A finished job
+ * that failed is released too and returns its status (APSP_ETIMEOUT when a
+ * bounded device wait of its solve expired, APSP_ENOMEM or APSP_ECUDA). bs_used (may be
  * NULL) receives the block size the job ran with.
  */
 apsp_status apsp_serve_poll(apsp_server* s, uint64_t job_id, float* D, int32_t* P, int* bs_used, int timeout_ms);

@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
     L.apsp_status_str.restype = ctypes.c_char_p
     L.apsp_fw_workspace_size.argtypes = [c_int, ctypes.POINTER(apsp_options)]
     L.apsp_fw_workspace_size.restype = c_size
+    L.apsp_fw_workspace_size_for.argtypes = [c_int, ctypes.POINTER(apsp_options), vp, vp]
+    L.apsp_fw_workspace_size_for.restype = c_size
     L.apsp_fw.argtypes = [vp, vp, vp, c_int, vp]
     L.apsp_fw.restype = c_int
     L.apsp_fw_ex.argtypes = [vp, vp, vp, c_int, ctypes.POINTER(apsp_options), vp, c_size,
@@ -132,6 +134,9 @@ def load(build_if_missing: bool = True):
         L.apsp_serve_create.restype = c_int
         L.apsp_serve_submit.argtypes = [vp, vp, c_int, ctypes.POINTER(ctypes.c_uint64)]
         L.apsp_serve_submit.restype = c_int
+        L.apsp_serve_submit_ex.argtypes = [vp, vp, c_int, ctypes.POINTER(apsp_options),
+                                           ctypes.POINTER(ctypes.c_uint64)]
+        L.apsp_serve_submit_ex.restype = c_int
         L.apsp_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, vp, ctypes.POINTER(c_int), c_int]
         L.apsp_serve_poll.restype = c_int
         L.apsp_serve_stats.argtypes = [vp, ctypes.POINTER(apsp_stats)]
@@ -192,6 +197,15 @@ def apsp_autotune_bs(n: int, stream=None) -> tuple[int, list[float]]:
 def apsp_fw_workspace_size(n: int, bs: int = 0, dtype: int = DTYPE_AUTO, validate: bool = True) -> int:
     o = _opts(bs, dtype, validate)
     return int(load().apsp_fw_workspace_size(int(n), ctypes.byref(o)))
+
+
+def apsp_fw_workspace_size_for(n: int, D: int, P: int, bs: int = 0, dtype: int = DTYPE_AUTO,
+                               validate: bool = True) -> int:
+    """apsp_fw_workspace_size_for: workspace bytes for these D and P device addresses (a D or P
+    that does not start on a 16-byte boundary needs a padded working copy)."""
+    o = _opts(bs, dtype, validate)
+    return int(load().apsp_fw_workspace_size_for(int(n), ctypes.byref(o), ctypes.c_void_p(int(D)),
+                                                 ctypes.c_void_p(int(P))))
 
 
 def apsp_fw(W: torch.Tensor, D: torch.Tensor, P: torch.Tensor, stream=None) -> None:
@@ -374,13 +388,20 @@ class Server:
         _check(L.apsp_serve_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots)), "apsp_serve_create")
         self._h = h
 
-    def submit(self, W: np.ndarray | torch.Tensor) -> int:
+    def submit(self, W: np.ndarray | torch.Tensor, bs: int | None = None, dtype: int | None = None,
+               flags: int = 0) -> int:
+        """apsp_serve_submit, or apsp_serve_submit_ex when bs, dtype or flags are given."""
         if isinstance(W, torch.Tensor):
             W = W.detach().cpu().numpy()
         W = np.ascontiguousarray(W, dtype=np.float32)
         jid = ctypes.c_uint64()
-        _check(load().apsp_serve_submit(self._h, W.ctypes.data, int(W.shape[0]), ctypes.byref(jid)),
-               "apsp_serve_submit")
+        if bs is None and dtype is None and not flags:
+            _check(load().apsp_serve_submit(self._h, W.ctypes.data, int(W.shape[0]), ctypes.byref(jid)),
+                   "apsp_serve_submit")
+        else:
+            o = _opts(bs or 0, DTYPE_AUTO if dtype is None else dtype, True, flags)
+            _check(load().apsp_serve_submit_ex(self._h, W.ctypes.data, int(W.shape[0]), ctypes.byref(o),
+                                               ctypes.byref(jid)), "apsp_serve_submit_ex")
         return int(jid.value)
 
     def poll(self, job_id: int, n: int, timeout_ms: int = -1, want_result: bool = True, out=None):

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -26,17 +27,28 @@
 
 namespace apsp {
 
-static int g_sm_count = 0;
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (dev >= 0 && dev < kMaxDevices) ? dev : -1;
+}
 
 int sm_count() {
-  if (g_sm_count == 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      g_sm_count = v;
-    else
-      g_sm_count = 152;
+  static std::atomic<int> cache[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return 152;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
   }
-  return g_sm_count;
+  return v;
 }
 
 static int elementwise_grid(size_t work) {
@@ -118,9 +130,13 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
   constexpr size_t sm2 = phase2_smem_bytes<T, BS>();
   constexpr size_t sm3 = std::is_same<T, F32T>::value ? minplus_f32_smem_bytes<BS>() : minplus_u16_smem_bytes<BS>();
   constexpr size_t sm3r = minplus_f32_real_smem_bytes<BS>();
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
+  // Function attributes belong to the device that was current when they were set.
+  static std::once_flag once[kMaxDevices];
+  static cudaError_t attr_errs[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  cudaError_t& attr_err = attr_errs[dev];
+  std::call_once(once[dev], [&attr_err] {
     cudaError_t e1 = cudaFuncSetAttribute(fw_phase2_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     const cudaError_t e0 =
         cudaFuncSetAttribute(fw_phase1_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
@@ -160,8 +176,8 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
           keep(launch_dependent(fw_pack_panels_f32_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const float*>(D), ld,
                                 nT, r, static_cast<const RoundMax*>(rm), graph_int, Apk, Bpk));
           ++tm.other;
-          keep(launch_dependent(fw_phase3_f32_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
-                                static_cast<const RoundMax*>(rm), graph_int, static_cast<const float*>(Apk),
+          keep(launch_dependent(fw_phase3_f32_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r, rm, graph_int,
+                                static_cast<const float*>(Apk),
                                 static_cast<const float*>(Bpk), kStaggerCycles, sms, wait_ns, (int)test_timeout));
         } else {
           // real-valued weights: B slices 64 columns wide, tiles of 128 x 64
@@ -170,7 +186,7 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
                                 static_cast<const float*>(D), ld, nT, r, static_cast<const RoundMax*>(rm), 0, Apk,
                                 Bpk));
           ++tm.other;
-          keep(launch_dependent(fw_phase3_f32_real_kernel<BS>, nT * nTc, 256, sm3r, s, D, P, ld, nT, r,
+          keep(launch_dependent(fw_phase3_f32_real_kernel<BS>, nT * nTc, 256, sm3r, s, D, P, ld, nT, r, rm,
                                 static_cast<const float*>(Apk), static_cast<const float*>(Bpk), kStaggerCycles, sms,
                                 wait_ns, (int)test_timeout));
         }
@@ -180,8 +196,8 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
         keep(launch_dependent(fw_pack_panels_u16_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const uint16_t*>(D), ld, nT,
                          r, Apk16, Bpk16));
         ++tm.other;
-        keep(launch_dependent(fw_phase3_u16_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r,
-                         static_cast<const RoundMax*>(rm), static_cast<const uint32_t*>(Apk16),
+        keep(launch_dependent(fw_phase3_u16_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r, rm,
+                         static_cast<const uint32_t*>(Apk16),
                          static_cast<const uint32_t*>(Bpk16), kStaggerCycles, sms, wait_ns, (int)test_timeout));
       }
       tm.mark(2);
@@ -245,6 +261,8 @@ static void layout(Plan& pl, bool p_in_place) {
 
 int padded_order(int n) { return ((n + kTile - 1) / kTile) * kTile; }
 
+size_t fw_fault_word_offset() { return kRoundMaxOffset + offsetof(RoundMax, fault); }
+
 }  // namespace apsp
 
 using namespace apsp;
@@ -293,26 +311,51 @@ static apsp_options default_options() {
 
 static bool valid_bs(int bs) { return bs == 32 || bs == 64 || bs == 128; }
 
-extern "C" size_t apsp_fw_workspace_size(int n, const apsp_options* opt) {
-  apsp_options o = opt ? *opt : default_options();
-  if (n < 1) return 0;
+namespace apsp {
+
+// Workspace plan of fw_exec: the solve runs in place in the caller's D (fp32
+// path) and P only when n is a multiple of 128 and that matrix starts on a
+// 16-byte boundary (the vector loads and bulk copies need it); otherwise the
+// workspace also holds a padded working copy.
+static Plan plan_for(int n, int bs, int dtype, const void* D, const void* P, bool* p_in_place) {
   Plan pl;
   pl.n = n;
   pl.n_pad = padded_order(n);
-  pl.bs = o.bs == 0 ? default_bs_for(n, APSP_DTYPE_F32) : o.bs;
-  if (!valid_bs(pl.bs)) return 0;
+  pl.bs = bs;
+  pl.dtype = dtype;
   const bool pad = pl.n_pad != n;
-  // F32 working set
-  pl.dtype = APSP_DTYPE_F32;
-  pl.in_place = !pad;
-  layout(pl, !pad);
-  size_t f32 = pl.ws_total;
-  if (o.dtype == APSP_DTYPE_F32) return f32;
-  pl.dtype = APSP_DTYPE_U16X2;
-  pl.bs = o.bs == 0 ? default_bs_for(n, APSP_DTYPE_U16X2) : o.bs;
-  pl.in_place = false;
-  layout(pl, !pad);
-  return std::max(f32, pl.ws_total);
+  *p_in_place = !pad && aligned16(P);
+  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad && aligned16(D);
+  layout(pl, *p_in_place);
+  return pl;
+}
+
+size_t fw_exec_workspace(int n, int bs, int dtype, const void* D, const void* P) {
+  bool p_in_place = false;
+  return plan_for(n, bs, dtype, D, P, &p_in_place).ws_total;
+}
+
+size_t fw_workspace_need(int n, const apsp_options* opt, const void* D, const void* P) {
+  apsp_options o = opt ? *opt : default_options();
+  if (n < 1 || n > 65536) return 0;
+  if (o.bs != 0 && !valid_bs(o.bs)) return 0;
+  size_t need = 0;
+  if (o.dtype != APSP_DTYPE_U16X2)
+    need = fw_exec_workspace(n, o.bs ? o.bs : default_bs_for(n, APSP_DTYPE_F32), APSP_DTYPE_F32, D, P);
+  if (o.dtype != APSP_DTYPE_F32)
+    need = std::max(need, fw_exec_workspace(n, o.bs ? o.bs : default_bs_for(n, APSP_DTYPE_U16X2),
+                                            APSP_DTYPE_U16X2, D, P));
+  return need;
+}
+
+}  // namespace apsp
+
+extern "C" size_t apsp_fw_workspace_size(int n, const apsp_options* opt) {
+  return fw_workspace_need(n, opt, nullptr, nullptr);  // null pointers count as aligned
+}
+
+extern "C" size_t apsp_fw_workspace_size_for(int n, const apsp_options* opt, const float* D, const int32_t* P) {
+  return fw_workspace_need(n, opt, D, P);
 }
 
 namespace apsp {
@@ -335,30 +378,11 @@ static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats*
   return APSP_OK;
 }
 
-size_t fw_exec_workspace(int n, int bs, int dtype) {
-  Plan pl;
-  pl.n = n;
-  pl.n_pad = padded_order(n);
-  pl.bs = bs;
-  pl.dtype = dtype;
-  const bool pad = pl.n_pad != n;
-  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad;
-  layout(pl, !pad);
-  return pl.ws_total;
-}
-
 // Run the block rounds with the arithmetic already chosen (no input scan).
 apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dtype, int graph_int, int flags,
                     void* workspace, size_t workspace_bytes, apsp_run_info* info, cudaStream_t s) {
-  Plan pl;
-  pl.n = n;
-  pl.n_pad = padded_order(n);
-  pl.bs = bs;
-  pl.dtype = dtype;
-  const bool pad = pl.n_pad != n;
-  const bool p_in_place = !pad && aligned16(P);
-  pl.in_place = (dtype == APSP_DTYPE_F32) && !pad && aligned16(D);
-  layout(pl, p_in_place);
+  bool p_in_place = false;
+  const Plan pl = plan_for(n, bs, dtype, D, P, &p_in_place);
   void* ws = workspace;
   bool own_ws = false;
   if (ws == nullptr) {
@@ -374,6 +398,7 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
   char* wsb = static_cast<char*>(ws);
   int32_t* Pw = p_in_place ? P : reinterpret_cast<int32_t*>(wsb + pl.ws_p);
   const size_t quads = (size_t)pl.n_pad * (pl.n_pad / 4);
+  RoundMax* rmax = reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset);
   PhaseTimer tm;
   tm.s = s;
   tm.on = (flags & APSP_FLAG_TIME_PHASES) != 0;
@@ -381,9 +406,9 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
   cudaError_t e = cudaSuccess;
   if (dtype == APSP_DTYPE_F32) {
     float* Dw = pl.in_place ? D : reinterpret_cast<float*>(wsb + pl.ws_d);
-    init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
+    init_f32_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad, &rmax->fault);
     ++aux;
-    e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset),
+    e = launch_rounds<F32T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, rmax,
                             graph_int, reinterpret_cast<float*>(wsb + pl.ws_pan), wsb + pl.ws_diag, flags);
     if (e == cudaSuccess && !pl.in_place) {
       copy_out_kernel<float><<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
@@ -391,9 +416,9 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
     }
   } else {
     uint16_t* Dw = reinterpret_cast<uint16_t*>(wsb + pl.ws_d);
-    init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad);
+    init_u16_kernel<<<elementwise_grid(quads), 256, 0, s>>>(W, n, Dw, Pw, pl.n_pad, &rmax->fault);
     ++aux;
-    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, reinterpret_cast<RoundMax*>(wsb + kRoundMaxOffset), 0,
+    e = launch_rounds<U16T>(Dw, Pw, pl.n_pad, pl.bs, s, tm, rmax, 0,
                             reinterpret_cast<float*>(wsb + pl.ws_pan), wsb + pl.ws_diag, flags);
     if (e == cudaSuccess) {
       widen_u16_kernel<<<elementwise_grid((size_t)n * n), 256, 0, s>>>(Dw, pl.n_pad, D, n);
@@ -432,6 +457,9 @@ apsp_status fw_run(const float* W, float* D, int32_t* P, int n, const apsp_optio
   if (!o.validate && o.dtype != APSP_DTYPE_F32) return APSP_EINVAL;
   if (n > 65536) return APSP_EINVAL;
   if (workspace && ((uintptr_t)workspace & 255) != 0) return APSP_EINVAL;
+  // A caller workspace must hold what either possible arithmetic needs for these D and P;
+  // checked before anything is enqueued.
+  if (workspace && workspace_bytes < fw_workspace_need(n, &o, D, P)) return APSP_ENOMEM;
   if (info) std::memset(info, 0, sizeof(*info));
 
   // Scan counters: the caller's workspace head, or a small stream-ordered buffer.

@@ -75,7 +75,8 @@ extern "C" apsp_status apsp_fw_noalloc(const float* W, float* D, int32_t* P, int
   }
   // per-phase timing creates CUDA events; this entry point creates nothing
   if (o.flags & APSP_FLAG_TIME_PHASES) return APSP_EINVAL;
-  const size_t need = apsp_fw_workspace_size(n, &o);
+  // sized for the D and P given (a misaligned D or P needs a working copy in the array)
+  const size_t need = apsp::fw_workspace_need(n, &o, D, P);
   if (need == 0) return APSP_EINVAL;
   if (need > (size_t)APSP_NOALLOC_SCRATCH_BYTES) return APSP_ENOMEM;  // too large for the fixed array
   void* scratch = nullptr;

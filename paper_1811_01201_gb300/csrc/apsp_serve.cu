@@ -15,9 +15,17 @@
 // returns the memory to the budget and admits more work.
 //
 // Each result equals what apsp_fw with default options returns for the same
-// graph: small graphs run with BS = 32 (the default block size for n <= 2048)
+// graph: small graphs run with BS = 32 (the default block size for n <= 512)
 // in fp32, which the 16-bit path reproduces bit for bit; large graphs use the
-// default block size and the same 16-bit eligibility rule.
+// default block size and the same 16-bit eligibility rule. A job submitted
+// with explicit options (apsp_serve_submit_ex) that the batched kernel does not
+// cover runs the single-graph path with them.
+//
+// Failure detection: a single-graph dispatch runs in a workspace of its own,
+// whose fault word the phase kernels set when a bounded wait expires. The
+// dispatch copies that word to host memory after its kernels, and the
+// completion callback fails the job with APSP_ETIMEOUT if it is set, so one
+// failing job never marks the jobs running beside it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,7 +95,8 @@ struct Job {
   int n = 0;
   int bs = 32;
   int dtype = APSP_DTYPE_F32;
-  bool small = true;
+  int flags = 0;      // APSP_FLAG_* of a job submitted with options (single-graph path only)
+  bool small = true;  // runs in a batched launch
   bool integral = false;
   size_t footprint = 0;
   float* hW = nullptr;
@@ -131,9 +140,10 @@ struct Dispatch {
   ServerImpl* srv = nullptr;
   int stream_idx = 0;
   std::vector<std::shared_ptr<Job>> jobs;
-  void* staging = nullptr;  // pinned descriptor table of a batch
+  void* staging = nullptr;  // pinned: descriptor table of a batch, or the fault word of a single-graph solve
   size_t staging_cls = 0;
   apsp_status status = APSP_OK;
+  bool check_fault = false;  // staging holds the solve's fault word, copied back after its kernels
 };
 
 static void CUDART_CB on_dispatch_done(void* arg) {
@@ -141,6 +151,8 @@ static void CUDART_CB on_dispatch_done(void* arg) {
   Dispatch* d = static_cast<Dispatch*>(arg);
   ServerImpl* s = d->srv;
   const double t = now_s();
+  if (d->status == APSP_OK && d->check_fault && *static_cast<volatile unsigned*>(d->staging) != 0u)
+    d->status = APSP_ETIMEOUT;  // a bounded device wait of this solve expired: its D and P are not valid
   {
     std::lock_guard<std::mutex> g(s->m);
     for (auto& j : d->jobs) {
@@ -157,7 +169,7 @@ static void CUDART_CB on_dispatch_done(void* arg) {
 static size_t job_footprint(int n, bool small, int bs, int dtype) {
   const size_t nn = (size_t)n * n;
   size_t f = nn * (sizeof(float) + sizeof(int32_t));
-  if (!small) f += fw_exec_workspace(n, bs, dtype);
+  if (!small) f += fw_exec_workspace(n, bs, dtype, nullptr, nullptr);
   return f + 4096;
 }
 
@@ -191,7 +203,24 @@ static void run_dispatch(ServerImpl* s, Dispatch* d) {
       status = batch_launch_async(tbl, count, st);
     } else {
       auto& j = d->jobs.front();
-      status = fw_exec(j->dD, j->dD, j->dP, j->n, j->bs, j->dtype, j->integral ? 1 : 0, 0, nullptr, 0, nullptr, st);
+      // own workspace, so that this solve's fault word is read back for this job alone
+      const size_t wsb = fw_exec_workspace(j->n, j->bs, j->dtype, j->dD, j->dP);
+      void* ws = nullptr;
+      if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) {
+        cudaGetLastError();
+        status = APSP_ENOMEM;
+      } else {
+        status = fw_exec(j->dD, j->dD, j->dP, j->n, j->bs, j->dtype, j->integral ? 1 : 0, j->flags, ws, wsb,
+                         nullptr, st);
+        if (status == APSP_OK) {
+          *static_cast<unsigned*>(d->staging) = 0u;
+          if (cudaMemcpyAsync(d->staging, static_cast<char*>(ws) + fw_fault_word_offset(), sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            status = APSP_ECUDA;
+          d->check_fault = status == APSP_OK;
+        }
+        cudaFreeAsync(ws, st);
+      }
     }
   }
   for (auto& j : d->jobs) {
@@ -272,6 +301,11 @@ static void scheduler(ServerImpl* s) {
           break;
         }
       } else {
+        d->staging = s->pool.get(sizeof(unsigned), &d->staging_cls);  // the solve's fault word
+        if (!d->staging) {
+          delete d;
+          break;
+        }
         d->jobs.push_back(s->admitted.front());
         s->admitted.erase(s->admitted.begin());
       }
@@ -330,9 +364,19 @@ extern "C" apsp_status apsp_serve_create(apsp_server** out, size_t hbm_budget_by
   return APSP_OK;
 }
 
-extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n, uint64_t* job_id) {
+extern "C" apsp_status apsp_serve_submit_ex(apsp_server* srv, const float* W, int n, const apsp_options* opt,
+                                            uint64_t* job_id) {
   if (!srv || !W || !job_id || n < 1 || n > 65536) return APSP_EINVAL;
   ServerImpl& s = srv->impl;
+  int want_bs = 0, want_dtype = APSP_DTYPE_AUTO, flags = 0;
+  if (opt) {
+    want_bs = opt->bs;
+    want_dtype = opt->dtype;
+    flags = opt->flags;
+    if ((want_bs != 0 && want_bs != 32 && want_bs != 64 && want_bs != 128) || want_dtype < APSP_DTYPE_AUTO ||
+        want_dtype > APSP_DTYPE_U16X2 || (flags & ~APSP_FLAG_TEST_PANEL_TIMEOUT) != 0)
+      return APSP_EINVAL;
+  }
   const size_t nn = (size_t)n * n;
   // host-side validation and 16-bit eligibility (same rule as apsp_fw)
   bool frac = false, bad = false;
@@ -349,17 +393,19 @@ extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n
       }
     }
   }
-  if (bad) {
+  const bool eligible = !frac && (double)mx * (double)(n - 1) < 65535.0;
+  if (bad || (want_dtype == APSP_DTYPE_U16X2 && !eligible)) {
     std::lock_guard<std::mutex> g(s.m);
     ++s.rejected;
     return APSP_EINVAL;
   }
   auto j = std::make_shared<Job>();
   j->n = n;
-  j->small = n <= kBatchMaxN;
-  j->bs = j->small ? 32 : apsp_default_bs(n);
-  const bool eligible = !frac && (double)mx * (double)(n - 1) < 65535.0;
-  j->dtype = (!j->small && eligible) ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32;
+  // the batched kernel covers fp32 (or equal 16-bit) results at BS = 32 without test flags
+  j->small = n <= kBatchMaxN && (want_bs == 0 || want_bs == 32) && want_dtype != APSP_DTYPE_U16X2 && flags == 0;
+  j->dtype = (!j->small && eligible && want_dtype != APSP_DTYPE_F32) ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32;
+  j->bs = j->small ? 32 : (want_bs ? want_bs : default_bs_for(n, j->dtype));
+  j->flags = flags;
   j->integral = !frac;
   j->footprint = job_footprint(n, j->small, j->bs, j->dtype);
   if (j->footprint > s.budget) {
@@ -395,6 +441,10 @@ extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n
   }
   s.cv_sched.notify_one();
   return APSP_OK;
+}
+
+extern "C" apsp_status apsp_serve_submit(apsp_server* srv, const float* W, int n, uint64_t* job_id) {
+  return apsp_serve_submit_ex(srv, W, n, nullptr, job_id);
 }
 
 extern "C" apsp_status apsp_serve_poll(apsp_server* srv, uint64_t job_id, float* D, int32_t* P, int* bs_used,

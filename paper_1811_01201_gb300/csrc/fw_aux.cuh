@@ -47,9 +47,11 @@ __global__ void scan_weights_kernel(const float* __restrict__ W, int n, WeightSt
 }
 
 // D (n_pad x n_pad) <- W (n x n) with a zero diagonal and INF padding;
-// P <- -1. One thread per 4 consecutive destination columns.
+// P <- -1; the solve's fault word <- 0. One thread per 4 consecutive
+// destination columns.
 __global__ void init_f32_kernel(const float* __restrict__ W, int n, float* __restrict__ D, int32_t* __restrict__ P,
-                                int n_pad) {
+                                int n_pad, unsigned* fault) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *fault = 0u;
   const size_t quads = (size_t)n_pad * (n_pad / 4);
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < quads; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / (n_pad / 4));
@@ -68,7 +70,8 @@ __global__ void init_f32_kernel(const float* __restrict__ W, int n, float* __res
 
 // 16-bit working matrix: D16 <- W (integers below 0xFFFF, INF -> 0xFFFF).
 __global__ void init_u16_kernel(const float* __restrict__ W, int n, uint16_t* __restrict__ D, int32_t* __restrict__ P,
-                                int n_pad) {
+                                int n_pad, unsigned* fault) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *fault = 0u;
   const size_t quads = (size_t)n_pad * (n_pad / 4);
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < quads; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / (n_pad / 4));

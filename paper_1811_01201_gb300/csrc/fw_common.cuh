@@ -49,15 +49,25 @@ struct U16T {
 // of phase 3) and its row-panel blocks to `b` (the B operand). fp32: largest
 // finite value as a bit pattern (for non-negative floats the integer order is
 // the value order). 16-bit: largest value with INF (0xFFFF) included.
+// `fault` is the solve's own fault word (zeroed by the init kernel, never by
+// the rounds): a bounded wait of this solve that expired sets a bit in it, so
+// a caller that runs several solves at once can tell which one failed.
 struct RoundMax {
   unsigned int a_bits;
   unsigned int b_bits;
+  unsigned int fault;
 };
 
-// Device-side fault word of this translation unit's kernels: a bounded wait
-// that expired sets a bit here instead of hanging; the host reads and clears it.
+// Device-side fault word of this translation unit's kernels, shared by every
+// solve on the device: a bounded wait that expired sets a bit here (and in the
+// solve's own word) instead of hanging; the host reads and clears it.
 constexpr unsigned kFaultPanelCopyTimeout = 1u;
 static __device__ unsigned int g_apsp_fault = 0;
+
+__device__ __forceinline__ void report_fault(RoundMax* rm, unsigned bit) {
+  atomicOr(&rm->fault, bit);
+  atomicOr(&g_apsp_fault, bit);
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;

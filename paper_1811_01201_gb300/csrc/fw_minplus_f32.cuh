@@ -95,7 +95,7 @@ __device__ __forceinline__ float floor_pos(float v) {
 template <int BS>
 __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __restrict__ P, size_t ld, int kb,
                                           int r0, int c0, bool keyed, float* As, float* Bs, uint64_t* bar,
-                                          unsigned long long wait_ns) {
+                                          unsigned long long wait_ns, RoundMax* rm) {
   constexpr float M = KeyParams<BS>::M;
   const float INF = f32_inf();
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -118,7 +118,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
   // The packed panel slices were requested by the kernel before the tile load;
   // the whole CTA goes on only if every thread saw them arrive in time.
   if (!__syncthreads_and(mbar_wait_phase0(bar, wait_ns))) {
-    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    if (tid == 0) report_fault(rm, kFaultPanelCopyTimeout);
     mbar_wait_phase0(bar, wait_ns);  // copies still in flight land before the CTA exits
     return;
   }
@@ -354,8 +354,7 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
 // CTA loads its tile, so the copies overlap the tile load.
 template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict__ D, int32_t* __restrict__ P,
-                                                               size_t ld, int nT, int r, const RoundMax* __restrict__ rm,
-                                                               int graph_int, const float* __restrict__ Apk,
+                                                               size_t ld, int nT, int r, RoundMax* rm, int graph_int, const float* __restrict__ Apk,
                                                                const float* __restrict__ Bpk, int stagger, int sms,
                                                                unsigned long long wait_ns, int no_copy) {
   extern __shared__ __align__(16) float sm[];
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_kernel(float* __restrict
       bulk_copy_g2s(Bs, Bpk + panel_slice_floats<BS>() * tc, slice_bytes, &bar);
     }
   }
-  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, As, Bs, &bar, wait_ns);
+  tile_body<BS>(D, P, ld, kb, r0, c0, keyed, As, Bs, &bar, wait_ns, rm);
 }
 
 // ---------------------------------------------------------------- real-valued graphs
@@ -417,7 +416,7 @@ constexpr size_t minplus_f32_real_smem_bytes() {
 
 template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __restrict__ D, int32_t* __restrict__ P,
-                                                                    size_t ld, int nT, int r,
+                                                                    size_t ld, int nT, int r, RoundMax* rm,
                                                                     const float* __restrict__ Apk,
                                                                     const float* __restrict__ Bpk, int stagger,
                                                                     int sms, unsigned long long wait_ns, int no_copy) {
@@ -457,7 +456,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
     for (int c = 0; c < 4; ++c) ds[a][c] = d[a][c];
   }
   if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
-    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    if (tid == 0) report_fault(rm, kFaultPanelCopyTimeout);
     mbar_wait_phase0(&bar, wait_ns);  // copies still in flight land before the CTA exits
     return;
   }

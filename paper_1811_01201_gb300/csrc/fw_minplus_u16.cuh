@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t*
 // expires sets kFaultPanelCopyTimeout and the CTA leaves its tile).
 template <int BS>
 __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restrict__ D, int32_t* __restrict__ P,
-                                                               size_t ld, int nT, int r,
-                                                               const RoundMax* __restrict__ rm,
+                                                               size_t ld, int nT, int r, RoundMax* rm,
                                                                const uint32_t* __restrict__ Apk,
                                                                const uint32_t* __restrict__ Bpk, int stagger, int sms,
                                                                unsigned long long wait_ns, int no_copy) {
@@ -186,7 +185,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
     for (int q = 0; q < 4; ++q) w[a][q] = old[a][q];
   }
   if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
-    if (tid == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    if (tid == 0) report_fault(rm, kFaultPanelCopyTimeout);
     mbar_wait_phase0(&bar, wait_ns);  // copies still in flight land before the CTA exits
     return;
   }

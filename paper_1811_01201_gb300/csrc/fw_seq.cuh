@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(LineShape<BS>::NT, LineShape<BS>::NT == 1024 ?
     p[e] = -1;
   }
   if (!__syncthreads_and(mbar_wait_phase0(&bar, wait_ns))) {
-    if (threadIdx.x == 0) atomicOr(&g_apsp_fault, kFaultPanelCopyTimeout);
+    if (threadIdx.x == 0) report_fault(rm, kFaultPanelCopyTimeout);
     mbar_wait_phase0(&bar, wait_ns);  // a copy still in flight lands before the CTA exits
     return;
   }

@@ -74,6 +74,25 @@ def test_workspace_size_formula():
         256 + up(2 * big * big) + up((big // 128) * 128 * 800) + up(8 * 128 * 132))
 
 
+def test_workspace_size_for_misaligned_matrices():
+    # the solve runs in place only in 16-byte-aligned D and P; a misaligned one needs its padded
+    # working copy (4 * n_pad^2 bytes) in the workspace, and apsp_fw_ex checks this before it
+    # enqueues anything
+    n, bs = 1024, 64
+    base = apsp.apsp_fw_workspace_size(n, bs=bs, dtype=apsp.DTYPE_F32)
+    assert apsp.apsp_fw_workspace_size_for(n, 0x10000, 0x20000, bs=bs, dtype=apsp.DTYPE_F32) == base
+    extra = 4 * n * n
+    assert apsp.apsp_fw_workspace_size_for(n, 0x10004, 0x20000, bs=bs, dtype=apsp.DTYPE_F32) == base + extra
+    assert apsp.apsp_fw_workspace_size_for(n, 0x10000, 0x20008, bs=bs, dtype=apsp.DTYPE_F32) == base + extra
+    assert apsp.apsp_fw_workspace_size_for(n, 0x10004, 0x20008, bs=bs, dtype=apsp.DTYPE_F32) == base + 2 * extra
+    # n not a multiple of 128: working copies either way, alignment changes nothing
+    m = 1000
+    assert apsp.apsp_fw_workspace_size_for(m, 0x10004, 0x20008, bs=bs, dtype=apsp.DTYPE_F32) == \
+        apsp.apsp_fw_workspace_size(m, bs=bs, dtype=apsp.DTYPE_F32)
+    # AUTO takes the larger of the two arithmetics for the same pointers
+    assert apsp.apsp_fw_workspace_size_for(n, 0x10004, 0x20000, bs=bs) >= base + extra
+
+
 def test_path_helper_matches_oracle_walk():
     import oracle
     from paper_1811_01201_gb300 import inputs

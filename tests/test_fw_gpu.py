@@ -266,7 +266,7 @@ def test_deterministic_repeats():
 
 # ---------------------------------------------------------------- full benchmark sizes (sampled)
 
-def _sampled_check(n, seed, lo, hi, density, kind, bs, n_src=6, n_pairs=20000, dtype=apsp.DTYPE_AUTO,
+def _sampled_check(n, seed, lo, hi, density, kind, bs, n_src=6, n_pairs=1_000_000, dtype=apsp.DTYPE_AUTO,
                    expect_dtype=None, expect_bs=None):
     Wd = inputs.dense_digraph(n, seed, lo, hi, density=density, kind=kind, device=DEV)
     D = torch.empty_like(Wd)

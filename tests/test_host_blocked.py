@@ -31,3 +31,20 @@ def test_ties_keep_the_earlier_k():
 
 def test_reports_its_thread_count():
     assert host_blocked.threads() >= 1
+
+
+@pytest.mark.parametrize("n,bs,lo,hi,density,kind", [
+    (1024, 64, 1, 1000, 0.5, "int"),    # the shape of the n = 8192 density-0.5 workload
+    (1024, 128, 1, 1000, 1.0, "int"),
+    (768, 64, 0, 1, 1.0, "real"),
+    (640, 128, 1, 15, 0.3, "int"),      # a 16-bit-eligible graph whose elements improve
+])
+def test_equals_blocked_oracle_at_larger_sizes(n, bs, lo, hi, density, kind):
+    # the whole-matrix GPU parity tests at the benchmark sizes take this implementation as the
+    # oracle (the serial one needs minutes there), so it is pinned here at sizes that span many
+    # blocks of every phase, with the workloads' weight distributions
+    W = inputs.dense_digraph(n, 7 * n + bs, lo, hi, density=density, kind=kind).numpy()
+    D, P = host_blocked.fw_blocked(W, bs)
+    Dr, Pr = oracle.fw_blocked(W, bs)
+    np.testing.assert_array_equal(D, Dr)
+    np.testing.assert_array_equal(P, Pr)

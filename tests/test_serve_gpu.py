@@ -143,3 +143,79 @@ def test_destroy_with_pending_work():
         D, P, _ = srv2.poll(j, Ws[0].shape[0], timeout_ms=60000)
         Da, Pa = _alone(Ws[0])
         assert np.array_equal(D, Da) and np.array_equal(P, Pa)
+
+
+def test_small_jobs_finish_while_an_earlier_large_job_is_on_the_device():
+    # Continuous batching: a request that arrives while a large solve runs is admitted, runs
+    # beside it and completes first. The large job (n = 12288, about 0.15 s of device work) is
+    # submitted first; once its kernels run, small graphs arrive and must all be done while the
+    # large one is still in flight. A server that ran jobs one at a time would finish the large
+    # job first.
+    big = inputs.dense_digraph(12288, 61, 1, 1000).numpy()
+    smalls = _graphs(8, 62, n_hi=256)
+    with apsp.Server(8 << 30, max_slots=16) as srv:
+        jb = srv.submit(big)
+        time.sleep(0.03)  # past the large job's host-to-device copy: its rounds are running
+        ids = [srv.submit(W) for W in smalls]
+        small_results = [srv.poll(j, W.shape[0], timeout_ms=60000) for j, W in zip(ids, smalls)]
+        assert srv.try_poll(jb, big.shape[0], timeout_ms=0, want_result=False) is None, \
+            "the large job finished before the small jobs that arrived after it"
+        D, P, bs = srv.poll(jb, big.shape[0], timeout_ms=120000)
+    for W, (Ds, Ps, _) in zip(smalls, small_results):
+        Da, Pa = _alone(W)
+        assert np.array_equal(Ds, Da) and np.array_equal(Ps, Pa)
+    Da, Pa = _alone(big)
+    assert np.array_equal(D, Da) and np.array_equal(P, Pa)
+
+
+def test_a_served_job_whose_device_wait_expires_fails_alone():
+    # Failure detection without a GPU fault: the test flag makes the job's bounded device waits
+    # expire (its kernels copy no panel slices; 20 ms per CTA wave), so its solve is invalid. The
+    # server reads that job's own fault word and fails it with APSP_ETIMEOUT; jobs running beside
+    # it return correct results, and the server keeps working.
+    bad = inputs.dense_digraph(640, 71, 1, 64).numpy()    # 16-bit path, 10 rounds of BS = 64
+    good = inputs.dense_digraph(700, 72, 1, 1000).numpy()  # fp32 path
+    smalls = _graphs(6, 73, n_hi=256)
+    try:
+        with apsp.Server(4 << 30, max_slots=16) as srv:
+            jbad = srv.submit(bad, flags=apsp.FLAG_TEST_PANEL_TIMEOUT)
+            jgood = srv.submit(good)
+            ids = [srv.submit(W) for W in smalls]
+            with pytest.raises(apsp.ApspError) as e:
+                srv.poll(jbad, bad.shape[0], timeout_ms=60000)
+            assert e.value.status == apsp.APSP_ETIMEOUT
+            D, P, _ = srv.poll(jgood, good.shape[0], timeout_ms=60000)
+            Da, Pa = _alone(good)
+            assert np.array_equal(D, Da) and np.array_equal(P, Pa)
+            for j, W in zip(ids, smalls):
+                Ds, Ps, _ = srv.poll(j, W.shape[0], timeout_ms=60000)
+                Da, Pa = _alone(W)
+                assert np.array_equal(Ds, Da) and np.array_equal(Ps, Pa)
+            # the same graph without the flag is served correctly afterwards
+            D, P, bs = srv.poll(srv.submit(bad), bad.shape[0], timeout_ms=60000)
+            Da, Pa = _alone(bad)
+            assert np.array_equal(D, Da) and np.array_equal(P, Pa)
+            st = srv.stats()
+            assert st.completed == len(smalls) + 2  # the failed job is not counted as completed
+    finally:
+        apsp.apsp_device_status(clear=True)  # the device-wide word saw the expired waits too
+
+
+def test_submit_with_options():
+    W = inputs.dense_digraph(300, 74, 1, 30).numpy()  # 16-bit eligible
+    with apsp.Server(1 << 30, max_slots=4) as srv:
+        for bs, dtype in ((64, apsp.DTYPE_F32), (128, apsp.DTYPE_U16X2), (32, None)):
+            D, P, bs_used = srv.poll(srv.submit(W, bs=bs, dtype=dtype), 300, timeout_ms=60000)
+            assert bs_used == bs
+            Dr, Pr = oracle.fw_blocked(W, bs)
+            np.testing.assert_array_equal(D, Dr)
+            np.testing.assert_array_equal(P, Pr)
+        with pytest.raises(apsp.ApspError) as e:
+            srv.submit(W, bs=48)
+        assert e.value.status == apsp.APSP_EINVAL
+        with pytest.raises(apsp.ApspError) as e:
+            srv.submit(W, flags=apsp.FLAG_TIME_PHASES)
+        assert e.value.status == apsp.APSP_EINVAL
+        with pytest.raises(apsp.ApspError) as e:
+            srv.submit(inputs.dense_digraph(300, 75, 1, 1000).numpy(), dtype=apsp.DTYPE_U16X2)
+        assert e.value.status == apsp.APSP_EINVAL

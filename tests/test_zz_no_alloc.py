@@ -90,3 +90,91 @@ def test_noalloc_rejects_sizes_beyond_the_array():
     o = apsp.apsp_options(64, apsp.DTYPE_F32, 1, apsp.FLAG_TIME_PHASES)
     assert L.apsp_fw_noalloc(W.data_ptr(), W.data_ptr(), W.data_ptr(), 128, ctypes.byref(o), None,
                              None) == apsp.APSP_EINVAL
+
+
+class _Mempool:
+    """Usage counters of the device's default stream-ordered memory pool, read through the CUDA
+    driver API (the pool is a driver object, whichever runtime copy asks)."""
+
+    RESERVED_MEM_CURRENT, USED_MEM_CURRENT, USED_MEM_HIGH = 5, 7, 8  # CUmemPool_attribute
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr: int) -> int:
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return int(v.value)
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+
+def test_noalloc_allocates_no_device_memory():
+    # The property the entry point exists for: a call takes nothing from the stream-ordered pool
+    # (not even briefly: the pool's high-water mark does not move) and nothing from the device's
+    # free memory. The first call on a device may load the library's module (with its fixed
+    # array); the checks start after it.
+    L = _lib()
+    n = 1024
+    Wd = inputs.dense_digraph(n, 14, 1, 1000, density=0.5, device=DEV)
+    D = torch.empty_like(Wd)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    o = apsp.apsp_options(64, apsp.DTYPE_AUTO, 1, 0)
+    s = torch.cuda.current_stream()
+
+    def call():
+        st = L.apsp_fw_noalloc(Wd.data_ptr(), D.data_ptr(), P.data_ptr(), n, ctypes.byref(o), None, s.cuda_stream)
+        torch.cuda.synchronize()
+        assert st == apsp.APSP_OK, apsp.status_str(st)
+
+    call()
+    pool = _Mempool()
+    for _ in range(2):
+        used, reserved = pool.get(pool.USED_MEM_CURRENT), pool.get(pool.RESERVED_MEM_CURRENT)
+        pool.reset_high()
+        free_before = torch.cuda.mem_get_info()[0]
+        call()
+        free_after = torch.cuda.mem_get_info()[0]
+        assert pool.get(pool.USED_MEM_HIGH) <= used, "the call took memory from the stream-ordered pool"
+        assert pool.get(pool.USED_MEM_CURRENT) == used and pool.get(pool.RESERVED_MEM_CURRENT) == reserved
+        assert free_after == free_before, "the device's free memory changed across the call"
+    # the same measurement sees the allocating entry point take its workspace from the pool
+    pool.reset_high()
+    used = pool.get(pool.USED_MEM_CURRENT)
+    apsp.apsp_fw_ex(Wd, D, P, bs=64)
+    torch.cuda.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) > used
+
+
+def test_noalloc_sizes_misaligned_matrices_before_enqueueing():
+    # a D that does not start on a 16-byte boundary needs a padded working copy in the fixed
+    # array; the entry point sizes for the D and P it is given. n = 2048: the copy fits and the
+    # result equals the allocating entry point's; n = 4096: it fits only when aligned, and the
+    # call is refused with APSP_ENOMEM before anything is enqueued (D keeps its contents).
+    L = _lib()
+    cap = L.apsp_noalloc_scratch_bytes()
+    o = apsp.apsp_options(64, apsp.DTYPE_F32, 1, 0)
+    for n in (2048, 4096):
+        assert apsp.apsp_fw_workspace_size(n, bs=64, dtype=apsp.DTYPE_F32) <= cap
+        Wd = inputs.dense_digraph(n, 15, 1, 1000, device=DEV)
+        buf = torch.full((n * n + 1,), -3.0, device=DEV)
+        Dm = buf[1:]  # 4-byte offset
+        P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+        need = apsp.apsp_fw_workspace_size_for(n, Dm.data_ptr(), P.data_ptr(), bs=64, dtype=apsp.DTYPE_F32)
+        assert need == apsp.apsp_fw_workspace_size(n, bs=64, dtype=apsp.DTYPE_F32) + 4 * n * n
+        st = L.apsp_fw_noalloc(Wd.data_ptr(), Dm.data_ptr(), P.data_ptr(), n, ctypes.byref(o), None,
+                               torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        if need > cap:
+            assert n == 4096 and st == apsp.APSP_ENOMEM
+            assert bool((Dm == -3.0).all())
+        else:
+            assert n == 2048 and st == apsp.APSP_OK, apsp.status_str(st)
+            Dr, Pr = _reference(Wd, 64, apsp.DTYPE_F32)
+            assert torch.equal(Dm.view(n, n), Dr) and torch.equal(P, Pr)
