@@ -39,11 +39,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Roofline denominators (unit counts x clock), from the issue rates that
-# csrc/probes/min_rates.cu measures on register operands: 152 SMs, one warp
-# instruction per clock per SM sub-partition (128 lanes/clk/SM). The FP32 min
-# issues at full rate, and the three-input min the compiler forms from two
-# successive mins at half rate, so one relaxation costs one min lane:
+# Roofline denominators (unit counts x clock). Issue rates measured with a
+# register-operand microbenchmark on a GB300 (relaxations per SM clock): 152
+# SMs, one warp instruction per clock per SM sub-partition (128 lanes/clk/SM).
+# The FP32 min issues at full rate, and the three-input min the compiler forms
+# from two successive mins at half rate, so one relaxation costs one min lane:
 # 128 relaxations/clk/SM. The fp32 pattern (add.rn.f32x2 + two mins per k pair)
 # also takes two issue slots per two relaxations, the same bound. The 16-bit
 # pattern (add.u16x2 + min.u16x2, two relaxations each) is issue-bound at the
@@ -52,13 +52,11 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 ALU_PEAK_F32_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
 ALU_PEAK_U16_TFLOPS = 2 * SMS * 128 * SM_MAX_MHZ * 1e6 / 1e12     # 80.54
-# What the fp32 instruction mix reaches with every operand in registers
-# (min_rates.cu: 106.1 relaxations/clk/SM, 8 independent chains per thread),
-# and what each phase-3 kernel's register tile per thread allows with no
-# memory instruction (8x8 for the integer kernel: 68.6; 8x4 for the real one: 78.7).
-PATTERN_CEILING_F32_TFLOPS = 2 * SMS * 106.1 * SM_MAX_MHZ * 1e6 / 1e12  # 66.77
-TILE_CEILING_F32_TFLOPS = {"int": 2 * SMS * 68.6 * SM_MAX_MHZ * 1e6 / 1e12,    # 43.17
-                           "real": 2 * SMS * 78.7 * SM_MAX_MHZ * 1e6 / 1e12}   # 49.53
+# What the fp32 phase-3 hot loop reaches with its panel pairs in shared memory and
+# no global traffic (8x8 register tile, 2 CTAs/SM; relaxations per SM clock from
+# ncu cycle counts): the instruction mix is bound by operand reads from the
+# register file, not by the min or add pipes (issue active 56%).
+HOT_LOOP_CEILING_F32_TFLOPS = 2 * SMS * 65.5 * SM_MAX_MHZ * 1e6 / 1e12  # 41.2
 
 
 def _hbm_peak():
@@ -184,10 +182,27 @@ def _oracle_sample(n_full: int, seed: int, lo: int, hi: int, n_sample: int, bs: 
 
 
 def cpu_baseline(args) -> dict:
-    dt, flops = _oracle_sample(args.n, args.seed, 1, 1000, args.cpu_sample_n, args.bs, args.kind)
-    return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
-            "sample": f"serial C blocked FW (BS={args.bs}) on the leading {args.cpu_sample_n}x{args.cpu_sample_n} "
-                      f"block of the n={args.n} workload, {dt:.1f} s"}
+    """The serial oracle's naive Floyd-Warshall (Section 3) on one host core: the whole n=512
+    workload, and a rate sample on the leading block of the timed workload; the full-size
+    times are extrapolated from the sample as t * (n / sample)^3 and labelled so."""
+    import oracle
+    from paper_1811_01201_gb300 import inputs
+    m = args.cpu_sample_n
+    W = inputs.dense_digraph(args.n, args.seed, 1, 1000, kind=args.kind, rows=(0, m))[:, :m].contiguous().numpy()
+    t0 = time.perf_counter()
+    oracle.fw_naive(W)
+    dt = time.perf_counter() - t0
+    W5 = inputs.dense_digraph(512, 1, 1, 100).numpy()
+    t1 = time.perf_counter()
+    oracle.fw_naive(W5)
+    dt5 = time.perf_counter() - t1
+    rate = 2.0 * m ** 3 / dt
+    return {"value": round(rate / 1e9, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
+            "sample": f"serial C naive FW (oracle_fw_naive) on a sample: the leading {m}x{m} block of the "
+                      f"n={args.n} workload, {dt:.1f} s; rate of that sample",
+            "n512_s": round(dt5, 4), "n512_gflops": round(2.0 * 512 ** 3 / dt5 / 1e9, 4),
+            "n8192_s_extrapolated": round(dt * (8192 / m) ** 3, 1),
+            f"n{args.n}_s_extrapolated": round(dt * (args.n / m) ** 3, 1)}
 
 
 def cpu_parallel_baseline(args) -> dict:
@@ -323,12 +338,10 @@ def run_gpu(args, rank: int, world: int):
             "frac": round(ph3_tflops / ALU_PEAK_F32_TFLOPS, 4) if ph3_tflops else None,
             "traffic": _traffic_from_profile(n, args.bs, args.kind),
             "kernel": f"fw_phase3_f32_real_kernel<{args.bs}>" if args.kind == "real" else f"fw_phase3_f32_kernel<{args.bs}>",
-            "peak_source": "derived: 152 SMs x 128 relaxations/clk (one min lane each; min rates measured by "
-                           "csrc/probes/min_rates.cu) x 2070 MHz x 2 flop",
-            "pattern_ceiling_tflops": round(PATTERN_CEILING_F32_TFLOPS, 2),
-            "frac_of_pattern_ceiling": round(ph3_tflops / PATTERN_CEILING_F32_TFLOPS, 4) if ph3_tflops else None,
-            "tile_ceiling_tflops": round(TILE_CEILING_F32_TFLOPS[args.kind], 2),
-            "frac_of_tile_ceiling": round(ph3_tflops / TILE_CEILING_F32_TFLOPS[args.kind], 4) if ph3_tflops else None,
+            "peak_source": "derived: 152 SMs x 128 relaxations/clk (one min lane each; FP32 min and "
+                           "three-input min issue rates measured on a GB300) x 2070 MHz x 2 flop",
+            "hot_loop_ceiling_tflops": round(HOT_LOOP_CEILING_F32_TFLOPS, 2),
+            "frac_of_hot_loop_ceiling": round(ph3_tflops / HOT_LOOP_CEILING_F32_TFLOPS, 4) if ph3_tflops else None,
             "phase_ms_per_step": [round(x / ph_steps, 3) for x in ph_ms],
             "phase_launches_per_step": [x // ph_steps for x in ph_launch],
             "phase_steps": ph_steps}
@@ -387,6 +400,19 @@ def run_gpu(args, rank: int, world: int):
                          "phase3_frac": round(ph3u / ALU_PEAK_U16_TFLOPS, 4)}
         del Wu, wsu
 
+    # The other single-graph workloads: n = 512 (integer weights U[1,100], dense), n = 32768 with
+    # real weights U(0,1], and a 16-bit-eligible graph whose elements improve (n = 16384,
+    # U[1,3], density 0.5: 3 * 16383 < 65535).
+    if args.extra_solves:
+        line["n512"] = run_solve_key(args, dev, 512, 1, 1, 100, 1.0, "int", 0, apsp.DTYPE_F32,
+                                     "dense digraph n=512, integer weights U[1,100]")
+        if n == 32768:
+            line["real32768"] = run_solve_key(args, dev, n, 4, 0, 1, 1.0, "real", 64, apsp.DTYPE_F32,
+                                              "dense digraph n=32768, real weights U(0,1]", D, P, traffic_kind="real")
+        line["u16x2_improving"] = run_solve_key(args, dev, 16384, 9, 1, 3, 0.5, "int", 0, apsp.DTYPE_AUTO,
+                                                "digraph n=16384, integer weights U[1,3], edge density 0.5 "
+                                                "(16-bit eligible; elements improve)", D, P)
+
     # End to end through apsp_fw_host: host pinned W in, host D and P out, every step.
     if args.e2e:
         Wh = W.cpu().pin_memory()
@@ -434,6 +460,50 @@ def run_gpu(args, rank: int, world: int):
         line["cpu_parallel_baseline"] = cpu_parallel_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_solve_key(args, dev, n, seed, lo, hi, density, kind, bs, dtype, workload, D=None, P=None,
+                  traffic_kind=None) -> dict:
+    """One more single-graph workload timed like the main one (device events around whole
+    solves, warm-ups first), with its phase times from one separate instrumented solve and the
+    phase-3 rate against the same ALU peak."""
+    import torch
+
+    import paper_1811_01201_gb300 as apsp
+    from paper_1811_01201_gb300 import inputs
+    W = inputs.dense_digraph(n, seed, lo, hi, density=density, kind=kind, device=dev)
+    if D is None or D.numel() != n * n:
+        D = torch.empty_like(W)
+        P = torch.empty((n, n), dtype=torch.int32, device=dev)
+    D, P = D.view(n, n), P.view(n, n)
+    ws = torch.empty(apsp.apsp_fw_workspace_size(n, bs=bs, dtype=dtype), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        apsp.apsp_fw_ex(W, D, P, bs=bs, dtype=dtype, workspace=ws)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        info = apsp.apsp_fw_ex(W, D, P, bs=bs, dtype=dtype, workspace=ws)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ip = apsp.apsp_fw_ex(W, D, P, bs=bs, dtype=dtype, workspace=ws, flags=apsp.FLAG_TIME_PHASES)
+    bsu = ip.bs_used
+    n_pad = ip.n_pad
+    ph3 = 2.0 * (n_pad - bsu) ** 2 * bsu * (n_pad // bsu) / (ip.phase_ms[2] * 1e-3) / 1e12 if ip.phase_ms[2] > 0 else 0
+    improved = int((P >= 0).sum())
+    out = {"workload": workload, "value": round(2.0 * n ** 3 / (ms * 1e-3) / 1e9, 2), "unit": "GFLOPS",
+           "ms_per_step": round(ms, 3), "steps": steps, "bs_used": bsu,
+           "dtype_used": "u16x2" if info.dtype_used == apsp.DTYPE_U16X2 else "f32",
+           "phase_ms": [round(x, 3) for x in ip.phase_ms], "phase3_tflops": round(ph3, 3),
+           "peak_tflops": round(ALU_PEAK_F32_TFLOPS, 2), "phase3_frac": round(ph3 / ALU_PEAK_F32_TFLOPS, 4),
+           "p_entries_set": improved, "gpu_launches_per_step": info.launches}
+    if traffic_kind is not None:
+        out["phase3_traffic_bytes_per_launch"] = _traffic_from_profile(n, bsu, traffic_kind)
+    del W, ws
+    return out
 
 
 def run_paths(args, dev, P, n: int, count: int, cap: int = 64, reps: int = 5) -> dict:
@@ -697,6 +767,8 @@ def main():
     ap.add_argument("--ref-sample-n", type=int, default=1536)
     ap.add_argument("--cpu-par-sample-n", type=int, default=6144)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-extra-solves", dest="extra_solves", action="store_false",
+                    help="skip the n=512, n=32768 real-weight and improving 16-bit solves")
     ap.add_argument("--no-c2", dest="autotune_c2", action="store_false",
                     help="skip the n=8192 density-0.5 solve with the autotuned block size")
     ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serve"],

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -18,6 +19,20 @@ namespace apsp {
 // Phase-3 tile height of a keyed graph before any autotuning.
 // (the autotuner's choice on the log-uniform [16, 512] mix: 32 rows up to n = 128, 64 above)
 int default_ph3_rows(int n) { return n <= 128 ? 32 : 64; }
+
+// The batched kernel's shared-memory limit, set once per device (function
+// attributes belong to the device that was current when they were set).
+static cudaError_t batched_kernel_attributes() {
+  static std::once_flag once[kMaxDevices];
+  static cudaError_t errs[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [dev] {
+    errs[dev] = cudaFuncSetAttribute(fw_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)batched_smem_bytes(kBMaxN));
+  });
+  return errs[dev];
+}
 
 // One CTA per graph: count negative / NaN off-diagonal weights.
 __global__ void scan_batch_kernel(const BatchGraph* __restrict__ graphs, int count, unsigned* bad) {
@@ -120,9 +135,7 @@ extern "C" apsp_status apsp_batch_create(const float* const* W, float* const* D,
     st = APSP_ECUDA;
   }
   if (st == APSP_OK) {
-    if (cudaFuncSetAttribute(fw_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batched_smem_bytes(kBMaxN)) != cudaSuccess)
-      st = APSP_ECUDA;
+    if (batched_kernel_attributes() != cudaSuccess) st = APSP_ECUDA;
     int per_sm = 0;
     if (st == APSP_OK &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, b->smem) != cudaSuccess)
@@ -252,12 +265,7 @@ apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cud
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, host_order, ord, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_q, 0, sizeof(BatchQueue), s);
   const size_t smem = batched_smem_bytes(n_max);
-  static bool attr_done = false;
-  if (e == cudaSuccess && !attr_done) {
-    e = cudaFuncSetAttribute(fw_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batched_smem_bytes(kBMaxN));
-    attr_done = e == cudaSuccess;
-  }
+  if (e == cudaSuccess) e = batched_kernel_attributes();
   if (e == cudaSuccess) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, smem);
