@@ -67,8 +67,10 @@ enum {
  *             n > 16384 and apsp_default_bs(n) otherwise (apsp_run_info.bs_used
  *             reports it); else 32, 64 or 128.
  *   dtype:    APSP_DTYPE_*. U16X2 is eligible only when every finite weight is
- *             an integer and max_w * (n - 1) < 65535, so that every path length
- *             fits in 16 bits; it gives bit-identical D and P to F32.
+ *             an integer and either max_w * (n - 1) < 65535, so that every
+ *             path length fits in 16 bits, or every off-diagonal edge is
+ *             present and max_w < 65535 (then no distance ever exceeds its
+ *             direct edge); it gives bit-identical D and P to F32.
  *             Requesting U16X2 for an ineligible W returns APSP_EINVAL.
  *   validate: 1 = scan W on the device for negative / NaN weights (and, for
  *             AUTO/U16X2, eligibility) before running; the call then

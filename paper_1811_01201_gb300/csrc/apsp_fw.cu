@@ -194,7 +194,7 @@ static cudaError_t launch_rounds_bs(typename T::store_t* D, int32_t* P, int n_pa
         uint32_t* Apk16 = reinterpret_cast<uint32_t*>(pan);
         uint32_t* Bpk16 = Apk16 + (size_t)nT * u16_slice_a_words<BS>();
         keep(launch_dependent(fw_pack_panels_u16_kernel<BS>, 2 * nT, 256, 0, s, static_cast<const uint16_t*>(D), ld, nT,
-                         r, Apk16, Bpk16));
+                              r, static_cast<const RoundMax*>(rm), Apk16, Bpk16));
         ++tm.other;
         keep(launch_dependent(fw_phase3_u16_kernel<BS>, nT * nT, 256, sm3, s, D, P, ld, nT, r, rm,
                          static_cast<const uint32_t*>(Apk16),
@@ -262,6 +262,15 @@ static void layout(Plan& pl, bool p_in_place) {
 int padded_order(int n) { return ((n + kTile - 1) / kTile) * kTile; }
 
 size_t fw_fault_word_offset() { return kRoundMaxOffset + offsetof(RoundMax, fault); }
+
+bool u16_eligible(bool all_integer, bool complete, float max_w, int n) {
+  if (!all_integer) return false;
+  // every simple path, at most n-1 edges, stays below INF = 65535
+  if ((double)max_w * (double)(n - 1) < 65535.0) return true;
+  // with every edge present, D[i][j] never exceeds W[i][j] <= max_w, so every stored value
+  // stays below 65535 and a saturated candidate never wins
+  return complete && max_w < 65535.0f;
+}
 
 }  // namespace apsp
 
@@ -371,7 +380,7 @@ static apsp_status scan_and_choose(const float* W, int n, int want, WeightStats*
   if (hs.n_negative || hs.n_nan) return APSP_EINVAL;
   float mx;
   std::memcpy(&mx, &hs.max_bits, sizeof(mx));
-  const bool eligible = hs.n_fraction == 0 && (double)mx * (double)(n - 1) < 65535.0;
+  const bool eligible = u16_eligible(hs.n_fraction == 0, hs.n_inf == 0, mx, n);
   if (want == APSP_DTYPE_U16X2 && !eligible) return APSP_EINVAL;
   *graph_int = hs.n_fraction == 0;
   *dtype_out = (want == APSP_DTYPE_F32) ? APSP_DTYPE_F32 : (eligible ? APSP_DTYPE_U16X2 : APSP_DTYPE_F32);

@@ -39,6 +39,11 @@ apsp_status fw_exec(const float* W, float* D, int32_t* P, int n, int bs, int dty
 // bounded device wait of that solve expired; zeroed by the solve's first kernel).
 size_t fw_fault_word_offset();
 
+// Eligibility of the exact 16-bit path: integer weights and either every
+// simple path length below 65535 (max_w * (n - 1) < 65535), or a complete
+// graph (no absent edge) with max_w < 65535.
+bool u16_eligible(bool all_integer, bool complete, float max_w, int n);
+
 // Library default block size for order n once the arithmetic is chosen.
 int default_bs_for(int n, int dtype);
 

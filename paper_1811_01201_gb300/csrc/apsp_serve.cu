@@ -10,7 +10,8 @@
 //     requests that arrive while earlier batches run are picked up by the next
 //     one instead of waiting for them to finish;
 //   * larger graphs run the single-graph blocked path on their own stream.
-// Work on different streams overlaps on the device. A host callback at the
+// Work on different streams overlaps on the device; the batched launches run on
+// high-priority streams, so that they get SMs while a large solve runs. A host callback at the
 // end of each dispatch stamps completion time and wakes the scheduler, which
 // returns the memory to the budget and admits more work.
 //
@@ -118,6 +119,8 @@ struct ServerImpl {
   int max_slots = 1;
   std::vector<cudaStream_t> streams;
   std::vector<bool> stream_busy;
+  std::vector<bool> stream_high;  // high-priority stream: small-graph batches
+  bool has_high = false;
   PinnedPool pool;
 
   std::mutex m;
@@ -279,15 +282,23 @@ static void scheduler(ServerImpl* s) {
       s->admitted.push_back(j);
       s->queue.pop_front();
     }
-    // dispatch onto free streams: all admitted small graphs as one batch, large graphs one each
+    // dispatch onto free streams: all admitted small graphs as one batch on a high-priority
+    // stream, large graphs one each on the others (a single stream takes both)
     std::vector<Dispatch*> todo;
     for (size_t si = 0; si < s->streams.size() && !s->admitted.empty(); ++si) {
       if (s->stream_busy[si]) continue;
+      const bool serves_small = s->stream_high[si] || !s->has_high;
+      const bool serves_large = !s->stream_high[si];
+      const bool have_small = std::any_of(s->admitted.begin(), s->admitted.end(),
+                                          [](const std::shared_ptr<Job>& j) { return j->small; });
+      const bool have_large = std::any_of(s->admitted.begin(), s->admitted.end(),
+                                          [](const std::shared_ptr<Job>& j) { return !j->small; });
+      const bool small_batch = serves_small && have_small;
+      if (!small_batch && !(serves_large && have_large)) continue;
       Dispatch* d = new Dispatch();
       d->srv = s;
       d->stream_idx = (int)si;
-      auto it = std::find_if(s->admitted.begin(), s->admitted.end(), [](const std::shared_ptr<Job>& j) { return j->small; });
-      if (it != s->admitted.end()) {
+      if (small_batch) {
         for (auto& j : s->admitted)
           if (j->small) d->jobs.push_back(j);
         s->admitted.erase(std::remove_if(s->admitted.begin(), s->admitted.end(),
@@ -306,8 +317,10 @@ static void scheduler(ServerImpl* s) {
           delete d;
           break;
         }
-        d->jobs.push_back(s->admitted.front());
-        s->admitted.erase(s->admitted.begin());
+        auto it = std::find_if(s->admitted.begin(), s->admitted.end(),
+                               [](const std::shared_ptr<Job>& j) { return !j->small; });
+        d->jobs.push_back(*it);
+        s->admitted.erase(it);
       }
       for (auto& j : d->jobs) j->state = kRunning;
       s->stream_busy[si] = true;
@@ -348,17 +361,30 @@ extern "C" apsp_status apsp_serve_create(apsp_server** out, size_t hbm_budget_by
     uint64_t thr = hbm_budget_bytes;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  // Half the streams (at least one, when there are two or more) run the batched launches of
+  // small graphs at the device's highest stream priority: a batched CTA needs a whole SM, and
+  // with the priority the block scheduler gives it the next SM that drains instead of another
+  // CTA of a large solve, so small requests overlap a running large one instead of waiting.
   const int ns = std::min(max_slots, 16);
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+    cudaGetLastError();
+    prio_low = prio_high = 0;
+  }
+  const int n_high = ns >= 2 ? ns / 2 : 0;
   for (int i = 0; i < ns; ++i) {
     cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    const bool high = i < n_high;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, high ? prio_high : prio_low) != cudaSuccess) {
       for (cudaStream_t x : s.streams) cudaStreamDestroy(x);
       delete srv;
       return APSP_ECUDA;
     }
     s.streams.push_back(st);
     s.stream_busy.push_back(false);
+    s.stream_high.push_back(high);
   }
+  s.has_high = n_high > 0;
   s.sched = std::thread(scheduler, &s);
   *out = srv;
   return APSP_OK;
@@ -379,7 +405,7 @@ extern "C" apsp_status apsp_serve_submit_ex(apsp_server* srv, const float* W, in
   }
   const size_t nn = (size_t)n * n;
   // host-side validation and 16-bit eligibility (same rule as apsp_fw)
-  bool frac = false, bad = false;
+  bool frac = false, bad = false, absent = false;
   float mx = 0.f;
   for (int i = 0; i < n; ++i) {
     const float* row = W + (size_t)i * n;
@@ -390,10 +416,12 @@ extern "C" apsp_status apsp_serve_submit_ex(apsp_server* srv, const float* W, in
       if (v < INFINITY) {
         frac |= v != std::floor(v);
         mx = v > mx ? v : mx;
+      } else {
+        absent = true;
       }
     }
   }
-  const bool eligible = !frac && (double)mx * (double)(n - 1) < 65535.0;
+  const bool eligible = u16_eligible(!frac, !absent, mx, n);
   if (bad || (want_dtype == APSP_DTYPE_U16X2 && !eligible)) {
     std::lock_guard<std::mutex> g(s.m);
     ++s.rejected;

@@ -12,15 +12,16 @@ struct WeightStats {
   unsigned int n_nan;        // NaN weights (off the diagonal)
   unsigned int n_fraction;   // finite weights that are not integers
   unsigned int max_bits;     // bit pattern of the largest finite weight (non-negative floats order as ints)
+  unsigned int n_inf;        // absent edges (+INF off the diagonal)
 };
 
 // Scan W (n x n, leading dimension n) for the validity and 16-bit
 // eligibility rules. Grid-stride, one atomic per counter per block.
 __global__ void scan_weights_kernel(const float* __restrict__ W, int n, WeightStats* st) {
-  __shared__ unsigned s_neg, s_nan, s_frac, s_max;
-  if (threadIdx.x == 0) { s_neg = 0; s_nan = 0; s_frac = 0; s_max = 0; }
+  __shared__ unsigned s_neg, s_nan, s_frac, s_max, s_inf;
+  if (threadIdx.x == 0) { s_neg = 0; s_nan = 0; s_frac = 0; s_max = 0; s_inf = 0; }
   __syncthreads();
-  unsigned neg = 0, nan = 0, frac = 0, mx = 0;
+  unsigned neg = 0, nan = 0, frac = 0, mx = 0, inf = 0;
   const size_t total = (size_t)n * n;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const size_t i = t / n, j = t - i * n;
@@ -31,17 +32,21 @@ __global__ void scan_weights_kernel(const float* __restrict__ W, int n, WeightSt
     if (v < f32_inf()) {
       if (v != floorf(v)) ++frac;
       mx = max(mx, (unsigned)__float_as_int(v));
+    } else {
+      ++inf;
     }
   }
   if (neg) atomicAdd(&s_neg, neg);
   if (nan) atomicAdd(&s_nan, nan);
   if (frac) atomicAdd(&s_frac, frac);
+  if (inf) atomicAdd(&s_inf, inf);
   atomicMax(&s_max, mx);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_neg) atomicAdd(&st->n_negative, s_neg);
     if (s_nan) atomicAdd(&st->n_nan, s_nan);
     if (s_frac) atomicAdd(&st->n_fraction, s_frac);
+    if (s_inf) atomicAdd(&st->n_inf, s_inf);
     atomicMax(&st->max_bits, s_max);
   }
 }

@@ -14,12 +14,15 @@
 //
 //  * integer-valued graphs whose round panels' largest finite values sum to
 //    at most a bound (phases 1-2 record the maxima): every operand is scaled
-//    by M = 2*BS and the A panel carries k+1 in the low bits (A' = M*a + k + 1,
-//    B' = M*b, D' = M*d; k+1 <= BS < M). The candidate keys M*(a+b) + k + 1
-//    are exact while below 2^24, so min over keys yields the minimum value
-//    and, among equal values, the smallest k -- while the old D (slot 0) wins
-//    ties, as the strict '<' requires. Slot 0 in the result means unchanged,
-//    so neither the old tile nor a search is needed: P comes for free.
+//    by M = 2*BS and the A panel carries k+1 in the low bits, all above an
+//    offset of 2^23 (A' = 2^23 + M*a + k + 1, B' = M*b, D' = 2^23 + M*d;
+//    k+1 <= BS < M). The candidate keys 2^23 + M*(a+b) + k + 1 are exact while
+//    below 2^24, so min over keys yields the minimum value and, among equal
+//    values, the smallest k -- while the old D (slot 0) wins ties, as the
+//    strict '<' requires. Slot 0 in the result means unchanged, so neither
+//    the old tile nor a search is needed: P comes for free. Every finite key
+//    lies in [2^23, 2^24), where the float's mantissa is the integer itself,
+//    so the slot and the value are read from the key's bits with integer ops.
 //  * rounds of integer graphs beyond that bound (rare): improved elements are
 //    found by comparing with the old D; where many improved every lane
 //    re-scans its own elements with k descending, else the warp re-evaluates
@@ -47,14 +50,29 @@ namespace apsp {
 
 constexpr int kDenseRescan = 384;  // improved elements per warp above which lanes re-scan their own
 
-// Key scale M = 2*BS (a power of two, so scaling is exact) and the largest
-// finite panel sum a + b for which every key M*(a+b) + BS stays below 2^24.
+// Key scale M = 2*BS (a power of two, so scaling is exact), the key offset
+// 2^23, and the largest finite panel sum a + b for which every key
+// 2^23 + M*(a+b) + BS stays below 2^24.
 template <int BS>
 struct KeyParams {
   static constexpr float M = 2.0f * BS;
-  static constexpr float bound = (float)(((1 << 24) - 2 * BS) / (2 * BS) - 16);
+  static constexpr int log2M = BS == 32 ? 6 : (BS == 64 ? 7 : 8);
+  static constexpr float off = 8388608.0f;  // 2^23
+  // Old values are keyed as min(2^23 + M*d, cap) with cap = 2^24 - M (slot 0): a D value too
+  // large for an exact key (or INF) reads as unchanged, and every finite candidate, below
+  // 2^23 + M*bound + BS < cap, still beats it.
+  static constexpr float cap = 16777216.0f - 2.0f * BS;
+  static constexpr float bound = (float)(((1 << 23) - 2 * BS) / (2 * BS) - 16);
   static_assert(BS == 32 || BS == 64 || BS == 128, "unsupported block size");
 };
+
+// B slices are stored with their 16-byte chunks swizzled (chunk c at
+// c ^ ((c >> 3) & 1)), so that the 16 lanes of a half warp, which read the
+// chunks 2*tx and 2*tx + 1 of their columns, fall on distinct bank groups in
+// pairs: two shared-memory wavefronts per 128-bit load instead of four.
+__host__ __device__ constexpr int bswz(int chunk) { return chunk ^ ((chunk >> 3) & 1); }
+// float offset of column j's k pair (element e = k & 1) in a B k-pair row
+__host__ __device__ constexpr int bcol(int j, int e) { return 4 * bswz(j >> 1) + 2 * (j & 1) + e; }
 
 // Panels are stored as k pairs: As[kp*kS2 + 2i + e] = A[i][2kp+e] and
 // Bs[kp*kS2 + 2j + e] = B[2kp+e][j], so one 128-bit load gives two rows' (or
@@ -81,6 +99,7 @@ __device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
 }
 
 __device__ __forceinline__ float pan(const float* S, int k, int x) { return S[(k >> 1) * kS2 + 2 * x + (k & 1)]; }
+__device__ __forceinline__ float pan_b(const float* S, int k, int x) { return S[(k >> 1) * kS2 + bcol(x, k & 1)]; }
 
 __device__ __forceinline__ int mp_row(int ty, int a) { return (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
 __device__ __forceinline__ int mp_col(int tx, int c) { return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
@@ -113,7 +132,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) d[a][c] *= M;
+      for (int c = 0; c < 8; ++c) d[a][c] = fminf(__fmaf_rn(d[a][c], M, KeyParams<BS>::off), KeyParams<BS>::cap);
   }
   // The packed panel slices were requested by the kernel before the tile load;
   // the whole CTA goes on only if every thread saw them arrive in time.
@@ -124,17 +143,18 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
   }
   // Hot loop: per k pair, one f32x2 add and two FMNMX per element.
   const float* Ap = As + ty * 8;
-  const float* Bp = Bs + tx * 8;
+  const float* Bp0 = Bs + 4 * bswz(2 * tx);      // columns tx*4, tx*4+1 (and +64 at +128)
+  const float* Bp1 = Bs + 4 * bswz(2 * tx + 1);  // columns tx*4+2, tx*4+3
 #pragma unroll 1
   for (int kp = 0; kp < BS / 2; ++kp) {
     const float4 a0 = *reinterpret_cast<const float4*>(Ap + kp * kS2);
     const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
     const float4 a2 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 128);
     const float4 a3 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 132);
-    const float4 b0 = *reinterpret_cast<const float4*>(Bp + kp * kS2);
-    const float4 b1 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 4);
-    const float4 b2 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 128);
-    const float4 b3 = *reinterpret_cast<const float4*>(Bp + kp * kS2 + 132);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bp0 + kp * kS2);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bp1 + kp * kS2);
+    const float4 b2 = *reinterpret_cast<const float4*>(Bp0 + kp * kS2 + 128);
+    const float4 b3 = *reinterpret_cast<const float4*>(Bp1 + kp * kS2 + 128);
     const float2 av[8] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}, {a1.z, a1.w},
                           {a2.x, a2.y}, {a2.z, a2.w}, {a3.x, a3.y}, {a3.z, a3.w}};
     const float2 bv[8] = {{b0.x, b0.y}, {b0.z, b0.w}, {b1.x, b1.y}, {b1.z, b1.w},
@@ -148,6 +168,11 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
       }
   }
   if (keyed) {
+    // Every key lies in [2^23, 2^24), so its bits are 0x4B000000 | (M*v + slot). A group of four
+    // without a slot is unchanged and costs two logic ops and a test; an improved element
+    // (always an exact candidate key) gets its value v and P = kb + slot - 1.
+    constexpr uint32_t kSlot = (uint32_t)(2 * BS) - 1u;
+    constexpr int kSh = KeyParams<BS>::log2M;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int gi = r0 + mp_row(ty, a);
@@ -156,24 +181,22 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
       for (int h = 0; h < 2; ++h) {
         const int gj = c0 + mp_col(tx, 4 * h);
         const bool band_c = (gj >= kb) && (gj < kb + BS);
-        float nv[4];
-        int sl[4];
-        bool any = false;
+        uint32_t kbits[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float key = d[a][4 * h + e];
-          const bool fin = key < INF;
-          const float v = floor_pos(key * (1.f / M));
-          sl[e] = fin ? (int)__fmaf_rn(-v, M, key) : 0;
-          nv[e] = fin ? v : INF;
-          any |= sl[e] != 0;
-        }
-        if (any && !band_r && !band_c) {
+        for (int e = 0; e < 4; ++e) kbits[e] = __float_as_uint(d[a][4 * h + e]);
+        if (((kbits[0] | kbits[1] | kbits[2] | kbits[3]) & kSlot) != 0u && !band_r && !band_c) {
           float* dp = D + (size_t)gi * ld + gj;
-          *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+          int32_t* pp = P + (size_t)gi * ld + gj;
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (sl[e] != 0) P[(size_t)gi * ld + gj + e] = kb + sl[e] - 1;
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t sl = kbits[e] & kSlot;
+            if (sl != 0u) {
+              // v = (M*v + slot) >> log2(M), rebuilt as the float 2^23 + v minus 2^23 (exact)
+              dp[e] = __fsub_rn(__uint_as_float(0x4B000000u | ((kbits[e] & 0x7FFFFFu) >> kSh)),
+                                KeyParams<BS>::off);
+              pp[e] = kb + (int)sl - 1;
+            }
+          }
         }
       }
     }
@@ -225,7 +248,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
         const float av[2] = {pan(As, k, ra0), pan(As, k, ra1)};
         float bv[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) bv[c] = pan(Bs, k, mp_col(tx, c));
+        for (int c = 0; c < 8; ++c) bv[c] = pan_b(Bs, k, mp_col(tx, c));
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -257,7 +280,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
 #pragma unroll
       for (int m = 0; m < BS / 32; ++m) {
         const int k = m * 32 + lane;
-        const float cand = __fadd_rn(pan(As, k, li), pan(Bs, k, lj));
+        const float cand = __fadd_rn(pan(As, k, li), pan_b(Bs, k, lj));
         const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
         if (eq && kstar == BS) kstar = m * 32 + __ffs(eq) - 1;
       }
@@ -276,7 +299,8 @@ __device__ __forceinline__ void spin_cycles(long long cycles) {
 // by fw_pack_panels_f32_kernel: slice tr of Apk holds A[i][k] (rows tr*128 ..
 // tr*128+127, the BS columns of block r) at [kp*kS2 + 2i + (k&1)], slice tc of
 // Bpk holds B[k][j] (the BS rows of block r, columns tc*128 ..) at
-// [kp*kS2 + 2j + (k&1)]. On keyed rounds A holds M*a + k + 1 and B holds M*b.
+// [kp*kS2 + bcol(j, k&1)] (swizzled chunks). On keyed rounds A holds
+// 2^23 + M*a + k + 1 and B holds M*b.
 template <int BS>
 __host__ __device__ constexpr size_t panel_slice_floats() {
   return (size_t)(BS / 2) * kS2;
@@ -318,7 +342,7 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
       const int i = (grp % (kTile / 8)) * 8 + ri;
       const int q4 = (grp / (kTile / 8)) * 4 + cq;
       const float4 v = *reinterpret_cast<const float4*>(D + (size_t)(r0 + i) * ld + kb + q4 * 4);
-      const float k0 = keyed ? (float)(q4 * 4 + 1) : 0.f;
+      const float k0 = keyed ? KeyParams<BS>::off + (float)(q4 * 4 + 1) : 0.f;  // exact below 2^24
       const float k1 = keyed ? k0 + 1.f : 0.f, k2 = keyed ? k0 + 2.f : 0.f, k3 = keyed ? k0 + 3.f : 0.f;
       *reinterpret_cast<float2*>(As + (2 * q4) * kS2 + 2 * i) = make_float2(fmaf(v.x, mb, k0), fmaf(v.y, mb, k1));
       *reinterpret_cast<float2*>(As + (2 * q4 + 1) * kS2 + 2 * i) = make_float2(fmaf(v.z, mb, k2), fmaf(v.w, mb, k3));
@@ -333,8 +357,9 @@ __global__ void __launch_bounds__(256) fw_pack_panels_f32_kernel(const float* __
       const int idx = tid + 256 * m, kp = idx / QW, q = idx % QW;
       const float4 x = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp) * ld + c0 + q * 4);
       const float4 y = *reinterpret_cast<const float4*>(D + (size_t)(kb + 2 * kp + 1) * ld + c0 + q * 4);
-      *reinterpret_cast<float4*>(Bs + kp * SB + q * 8) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
-      *reinterpret_cast<float4*>(Bs + kp * SB + q * 8 + 4) = make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
+      *reinterpret_cast<float4*>(Bs + kp * SB + 4 * bswz(2 * q)) = make_float4(x.x * mb, y.x * mb, x.y * mb, y.y * mb);
+      *reinterpret_cast<float4*>(Bs + kp * SB + 4 * bswz(2 * q + 1)) =
+          make_float4(x.z * mb, y.z * mb, x.w * mb, y.w * mb);
     }
   }
 }
@@ -462,7 +487,8 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
   }
   uint32_t tag[4] = {0u, 0u, 0u, 0u};  // element e = a*4 + c: bits 4*(e&7) of tag[e>>3]
   const float* Ap = As + ty * 8;
-  const float* Bp = Bs + tx * 8;
+  const float* Bp0 = Bs + 4 * bswz(2 * tx);
+  const float* Bp1 = Bs + 4 * bswz(2 * tx + 1);
 #pragma unroll 1
   for (int g = 0; g < NG; ++g) {
 #pragma unroll 1
@@ -472,8 +498,8 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
       const float4 a1 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 4);
       const float4 a2 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 128);
       const float4 a3 = *reinterpret_cast<const float4*>(Ap + kp * kS2 + 132);
-      const float4 b0 = *reinterpret_cast<const float4*>(Bp + kp * kRealSB);
-      const float4 b1 = *reinterpret_cast<const float4*>(Bp + kp * kRealSB + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bp0 + kp * kRealSB);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bp1 + kp * kRealSB);
       const float2 av[8] = {{a0.x, a0.y}, {a0.z, a0.w}, {a1.x, a1.y}, {a1.z, a1.w},
                             {a2.x, a2.y}, {a2.z, a2.w}, {a3.x, a3.y}, {a3.z, a3.w}};
       const float2 bv[4] = {{b0.x, b0.y}, {b0.z, b0.w}, {b1.x, b1.y}, {b1.z, b1.w}};
@@ -529,7 +555,7 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_f32_real_kernel(float* __res
 #pragma unroll
         for (int u = 0; u < kRealGroup; ++u)
           c2[u] = fadd2_rn(*reinterpret_cast<const float2*>(As + (kp0 + u) * kS2 + 2 * qi),
-                           *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kRealSB + 2 * qj));
+                           *reinterpret_cast<const float2*>(Bs + (kp0 + u) * kRealSB + bcol(qj, 0)));
         int kstar = BS;
 #pragma unroll
         for (int u = kRealGroup - 1; u >= 0; --u) {

@@ -13,10 +13,19 @@
 // at most 0xFFFF; otherwise (typically while panels still hold INF) the round
 // uses the saturating form sat(a + b) = min(a, ~b) + b (one more min per pair).
 //
-// P is recovered as in the fp32 generic path: an element improved iff its new
-// value is below the old one (kept in registers); a warp then re-evaluates its
-// BS candidates, one k per lane, and takes the first k whose saturated sum
-// equals the new value.
+// P comes, as on the fp32 path, from keys where the round allows them: when
+// every panel value of the round is finite and small enough (a + b below
+// 65536 / M - 1 with M = 2*BS; phases 1-2 record the maxima), every operand is
+// scaled by M inside its 16-bit lane and the A panel carries k+1 in the low
+// bits (A' = M*a + k + 1, B' = M*b, D' = M*min(d, T) with T = 65536/M - 1).
+// The same add.u16x2 + min.u16x2 loop then yields, per element, the minimum
+// value and the smallest k attaining it, while the old value (slot 0) wins
+// ties; an old value clamped to T (INF included) reads as unchanged, and every
+// finite candidate, at most M*(T-2) + BS, still beats it. Slot 0 means
+// unchanged. Other rounds (an INF or a large value in the panels) find the
+// improved elements by comparing with the old tile (kept in registers); a
+// warp then re-evaluates its BS candidates, one k per lane, and takes the
+// first k whose saturated sum equals the new value.
 //
 // Tiling: 128 x 128 output tile per CTA of 256 threads; each thread owns 8
 // rows (ty*4+{0..3}, 64+ty*4+{0..3}) x 8 consecutive columns (tx*8 ..), i.e.
@@ -33,6 +42,25 @@ namespace apsp {
 
 constexpr int kSstA16 = kTile + 4;      // words per transposed-A row
 constexpr int kSstB16 = kTile / 2 + 4;  // words per B row (two uint16 per word)
+
+// 16-bit keys of phase 3 (see the top of this file): scale M = 2*BS, clamp T,
+// and the largest panel sum a + b of a keyed round.
+template <int BS>
+struct Key16 {
+  static constexpr uint32_t M = 2u * BS;
+  static constexpr int log2M = BS == 32 ? 6 : (BS == 64 ? 7 : 8);
+  static constexpr uint32_t T = 65536u / M - 1u;
+  static constexpr uint32_t bound = T - 2u;
+  static constexpr uint32_t T2 = T | (T << 16);                                // clamp, both lanes
+  static constexpr uint32_t slot2 = (M - 1u) | ((M - 1u) << 16);               // slot bits, both lanes
+  static constexpr uint32_t val2 = ((0xFFFFu >> log2M)) | ((0xFFFFu >> log2M) << 16);  // value bits after >> log2M
+};
+
+// Keyed 16-bit round: the round's panel maxima (INF = 0xFFFF included) sum to at most the bound.
+template <int BS>
+__device__ __forceinline__ bool round_keyed16(const RoundMax* rm) {
+  return rm->a_bits + rm->b_bits <= Key16<BS>::bound;
+}
 
 template <int BS>
 constexpr size_t minplus_u16_smem_bytes() {
@@ -97,10 +125,13 @@ __device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint
 // 2q .. 2q+1]).
 template <int BS>
 __global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t* __restrict__ D, size_t ld, int nT,
-                                                                 int r, uint32_t* __restrict__ Apk,
+                                                                 int r, const RoundMax* __restrict__ rm,
+                                                                 uint32_t* __restrict__ Apk,
                                                                  uint32_t* __restrict__ Bpk) {
   pdl_prologue();
   const int kb = r * BS, tid = threadIdx.x;
+  const bool keyed = round_keyed16<BS>(rm);  // every panel value is then at most the bound: no lane overflows
+  constexpr int sh = Key16<BS>::log2M;
   if ((int)blockIdx.x < nT) {
     // 128 rows x BS uint16 (BS/8 uint4 per row), transposed + duplicated.
     const int r0 = blockIdx.x * kTile;
@@ -115,9 +146,14 @@ __global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t*
       const uint32_t h[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const uint32_t lo = h[e] & 0xFFFF, hi = h[e] >> 16;
-        As[(q8 * 8 + 2 * e) * kSstA16 + i] = lo | (lo << 16);
-        As[(q8 * 8 + 2 * e + 1) * kSstA16 + i] = hi | (hi << 16);
+        const int k0 = q8 * 8 + 2 * e;
+        uint32_t lo = h[e] & 0xFFFF, hi = h[e] >> 16;
+        if (keyed) {
+          lo = (lo << sh) + (uint32_t)(k0 + 1);
+          hi = (hi << sh) + (uint32_t)(k0 + 2);
+        }
+        As[k0 * kSstA16 + i] = lo | (lo << 16);
+        As[(k0 + 1) * kSstA16 + i] = hi | (hi << 16);
       }
     }
   } else {
@@ -127,7 +163,10 @@ __global__ void __launch_bounds__(256) fw_pack_panels_u16_kernel(const uint16_t*
 #pragma unroll
     for (int m = 0; m < BS / 16; ++m) {
       const int idx = tid + 256 * m, k = idx >> 4, q = idx & 15;
-      const uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
+      uint4 v = *reinterpret_cast<const uint4*>(D + (size_t)(kb + k) * ld + c0 + q * 8);
+      if (keyed) {  // both lanes below 65536 / M: the shift scales each lane without spilling
+        v.x <<= sh; v.y <<= sh; v.z <<= sh; v.w <<= sh;
+      }
       *reinterpret_cast<uint4*>(Bs + k * kSstB16 + q * 4) = v;
     }
   }
@@ -154,8 +193,10 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
   const int r0 = tr * kTile, c0 = tc * kTile;
   if (r0 >= kb && r0 + kTile <= kb + BS) return;
   if (c0 >= kb && c0 + kTile <= kb + BS) return;
-  // the round's panel maxima (INF included) decide whether a wrapping add is safe
+  // the round's panel maxima (INF included) decide whether a wrapping add is safe, and whether
+  // the round runs on keys
   const bool sat = rm->a_bits + rm->b_bits > 0xFFFFu;
+  const bool keyed = round_keyed16<BS>(rm);
   if (stagger > 0 && (int)blockIdx.x >= sms && (int)blockIdx.x < 2 * sms) {
     const long long t0 = clock64();
     while (clock64() - t0 < stagger) {
@@ -190,6 +231,34 @@ __global__ void __launch_bounds__(256, 2) fw_phase3_u16_kernel(uint16_t* __restr
     return;
   }
 
+  if (keyed) {
+    constexpr int sh = Key16<BS>::log2M;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[a][q] = vmin16(old[a][q], Key16<BS>::T2) << sh;  // slot 0
+    minplus_u16_loop<BS, false>(w, As + ty * 4, Bs + tx * 4);
+    // slot bits name the first k of each improved element; others keep their old value
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int gi = r0 + mp_row(ty, a);
+      const int gj = c0 + tx * 8;
+      if ((gi >= kb && gi < kb + BS) || (gj >= kb && gj < kb + BS)) continue;
+      const uint32_t any = (w[a][0] | w[a][1] | w[a][2] | w[a][3]) & Key16<BS>::slot2;
+      if (any == 0u) continue;
+      uint32_t nw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t sl = w[a][q] & Key16<BS>::slot2;
+        const uint32_t m = (sl & 0xFFFFu ? 0x0000FFFFu : 0u) | (sl >> 16 ? 0xFFFF0000u : 0u);
+        nw[q] = (((w[a][q] >> sh) & Key16<BS>::val2) & m) | (old[a][q] & ~m);
+        if (sl & 0xFFFFu) P[(size_t)gi * ld + gj + 2 * q] = kb + (int)(sl & 0xFFFFu) - 1;
+        if (sl >> 16) P[(size_t)gi * ld + gj + 2 * q + 1] = kb + (int)(sl >> 16) - 1;
+      }
+      *reinterpret_cast<uint4*>(D + (size_t)gi * ld + gj) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    }
+    return;
+  }
   if (sat)
     minplus_u16_loop<BS, true>(w, As + ty * 4, Bs + tx * 4);
   else

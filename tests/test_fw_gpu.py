@@ -67,9 +67,12 @@ def test_f32_large_distances_take_generic_path():
 
 
 @pytest.mark.parametrize("bs", [32, 64, 128])
-def test_f32_keys_near_exactness_bound(bs):
-    # integer distances close to the largest panel sum the exact-key path accepts for this BS
-    hi = {32: 120000, 64: 60000, 128: 30000}[bs]
+@pytest.mark.parametrize("scale", [1, 2])
+def test_f32_keys_near_exactness_bound(bs, scale):
+    # integer distances close to the largest panel sum the exact-key path of phase 3 accepts for
+    # this BS (keys 2^23 + 2*BS*(a+b) + k + 1 below 2^24: a + b <= 131055, 65519, 32751), and
+    # twice that, where rounds fall back to the generic search
+    hi = {32: 60000, 64: 30000, 128: 15000}[bs] * scale
     W = inputs.dense_digraph(300, seed=40 + bs, lo=hi // 2, hi=hi, density=0.4)
     D, P, _ = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
     _expect_exact(W, D, P, bs)
@@ -104,13 +107,30 @@ def test_u16_bound_edge():
     D, P, info = _run(W, bs=32)
     assert info.dtype_used == apsp.DTYPE_U16X2  # 255 * 256 = 65280 < 65535
     _expect_exact(W, D, P, 32)
-    W[0, 1] = 300.0  # 300 * 256 = 76800: not eligible
+    W[0, 1] = 300.0  # 300 * 256 = 76800, but the graph is complete: still eligible
+    D, P, info = _run(W, bs=32)
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    _expect_exact(W, D, P, 32)
+    W[5, 9] = INF  # one absent edge: the path-length rule alone decides, and 76800 >= 65535
     D, P, info = _run(W, bs=32)
     assert info.dtype_used == apsp.DTYPE_F32
     _expect_exact(W, D, P, 32)
     with pytest.raises(apsp.ApspError) as e:
         _run(W, bs=32, dtype=apsp.DTYPE_U16X2)
     assert e.value.status == apsp.APSP_EINVAL
+
+
+@pytest.mark.parametrize("n,hi,bs", [(600, 1000, 64), (513, 65534, 32), (1000, 30000, 128)])
+def test_u16_path_on_complete_graphs(n, hi, bs):
+    # complete graphs: no distance exceeds its direct edge, so integer weights below 65535 are
+    # eligible at any n (max_w * (n - 1) is far above 65535 here); D and P equal the fp32 path's
+    W = inputs.dense_digraph(n, seed=3500 + n, lo=1, hi=hi)
+    D, P, info = _run(W, bs=bs, dtype=apsp.DTYPE_AUTO)
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    _expect_exact(W, D, P, bs)
+    D2, P2, info2 = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    np.testing.assert_array_equal(D, D2)
+    np.testing.assert_array_equal(P, P2)
 
 
 def test_u16_long_chain_saturation():

@@ -147,11 +147,11 @@ def test_destroy_with_pending_work():
 
 def test_small_jobs_finish_while_an_earlier_large_job_is_on_the_device():
     # Continuous batching: a request that arrives while a large solve runs is admitted, runs
-    # beside it and completes first. The large job (n = 12288, about 0.15 s of device work) is
-    # submitted first; once its kernels run, small graphs arrive and must all be done while the
-    # large one is still in flight. A server that ran jobs one at a time would finish the large
-    # job first.
-    big = inputs.dense_digraph(12288, 61, 1, 1000).numpy()
+    # beside it and completes first. The large job (n = 12288, fp32 path, about 0.15 s of device
+    # work) is submitted first; once its kernels run, small graphs arrive and must all be done
+    # while the large one is still in flight. A server that ran jobs one at a time would finish
+    # the large job first.
+    big = inputs.dense_digraph(12288, 61, 1, 1000, density=0.95).numpy()
     smalls = _graphs(8, 62, n_hi=256)
     with apsp.Server(8 << 30, max_slots=16) as srv:
         jb = srv.submit(big)
