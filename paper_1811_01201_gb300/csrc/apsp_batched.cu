@@ -16,9 +16,9 @@
 
 namespace apsp {
 
-// Phase-3 tile height of a keyed graph before any autotuning.
-// (the autotuner's choice on the log-uniform [16, 512] mix: 32 rows up to n = 128, 64 above)
-int default_ph3_rows(int n) { return n <= 128 ? 32 : 64; }
+// Phase-3 tile of a keyed graph before any autotuning, by its height: 32 (32 x 64 tiles) up to
+// n = 96, 64 (64 x 64) up to n = 256, 128 (128 x 64) above.
+int default_ph3_rows(int n) { return n <= 96 ? 32 : (n <= 256 ? 64 : 128); }
 
 // The batched kernel's shared-memory limit, set once per device (function
 // attributes belong to the device that was current when they were set).
@@ -64,7 +64,7 @@ struct apsp_batch {
   BatchQueue* d_queue = nullptr;
   int count = 0;
   int n_max = 0;
-  int ldp = 0;
+  int sp = 0;
   size_t smem = 0;
   int grid = 0;
   std::vector<BatchGraph> hg;  // host copy of the descriptor table
@@ -110,7 +110,7 @@ extern "C" apsp_status apsp_batch_create(const float* const* W, float* const* D,
   b->order = order;
   b->count = count;
   b->n_max = n_max;
-  b->ldp = batched_ldp(n_max);
+  b->sp = batched_sp(n_max);
   b->smem = batched_smem_bytes(n_max);
   if (cudaMalloc(&b->d_graphs, sizeof(BatchGraph) * count) != cudaSuccess ||
       cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
@@ -155,7 +155,7 @@ extern "C" apsp_status apsp_batch_launch(apsp_batch* b, void* stream) {
   if (!b) return APSP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), s) != cudaSuccess) return APSP_ECUDA;
-  fw_batched_kernel<<<b->grid, kBThreads, b->smem, s>>>(b->d_graphs, b->d_order, b->count, b->d_queue, b->ldp, 0);
+  fw_batched_kernel<<<b->grid, kBThreads, b->smem, s>>>(b->d_graphs, b->d_order, b->count, b->d_queue, b->sp, 0);
   return cudaGetLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
 }
 
@@ -201,7 +201,7 @@ extern "C" apsp_status apsp_batch_autotune(apsp_batch* b, int* rows_out, void* s
       for (int rep = 0; rep < 3 && st == APSP_OK; ++rep) {  // the first run warms up
         cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), s);
         cudaEventRecord(e0, s);
-        fw_batched_kernel<<<grid, kBThreads, b->smem, s>>>(b->d_graphs, d_sub, cnt, b->d_queue, b->ldp, rows);
+        fw_batched_kernel<<<grid, kBThreads, b->smem, s>>>(b->d_graphs, d_sub, cnt, b->d_queue, b->sp, rows);
         cudaEventRecord(e1, s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
@@ -270,7 +270,7 @@ apsp_status batch_launch_async(const BatchGraphDesc* host_graphs, int count, cud
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_kernel, kBThreads, smem);
     const int grid = std::max(1, std::min(count, std::max(1, per_sm) * sm_count()));
-    fw_batched_kernel<<<grid, kBThreads, smem, s>>>(d_graphs, d_order, count, d_q, batched_ldp(n_max), 0);
+    fw_batched_kernel<<<grid, kBThreads, smem, s>>>(d_graphs, d_order, count, d_q, batched_sp(n_max), 0);
     e = cudaGetLastError();
   }
   cudaFreeAsync(buf, s);

@@ -514,31 +514,82 @@ extern "C" apsp_status apsp_device_status(int clear) {
   return (v & kFaultPanelCopyTimeout) ? APSP_ETIMEOUT : APSP_OK;
 }
 
+namespace apsp {
+
+// Streams that carry apsp_fw_host's copies in row chunks, so that several copy
+// engines move one matrix at once (created once per device, never destroyed).
+constexpr int kCopyStreams = 4;
+static cudaError_t copy_streams(cudaStream_t** out) {
+  static std::once_flag once[kMaxDevices];
+  static cudaStream_t streams[kMaxDevices][kCopyStreams];
+  static cudaError_t errs[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [dev] {
+    errs[dev] = cudaSuccess;
+    for (int c = 0; c < kCopyStreams && errs[dev] == cudaSuccess; ++c)
+      errs[dev] = cudaStreamCreateWithFlags(&streams[dev][c], cudaStreamNonBlocking);
+  });
+  *out = streams[dev];
+  return errs[dev];
+}
+
+// Copy `rows` rows of `row_bytes` bytes in kCopyStreams row chunks, each on its
+// own stream, ordered after everything enqueued on `s` so far; `s` then waits
+// for all chunks. ev: kCopyStreams + 1 events.
+static cudaError_t chunked_copy(void* dst, const void* src, size_t rows, size_t row_bytes, cudaMemcpyKind kind,
+                                cudaStream_t s, cudaStream_t* cs, cudaEvent_t* ev) {
+  cudaError_t e = cudaEventRecord(ev[kCopyStreams], s);
+  const size_t per = (rows + kCopyStreams - 1) / kCopyStreams;
+  for (int c = 0; c < kCopyStreams && e == cudaSuccess; ++c) {
+    const size_t r0 = std::min(rows, (size_t)c * per), r1 = std::min(rows, r0 + per);
+    e = cudaStreamWaitEvent(cs[c], ev[kCopyStreams], 0);
+    if (e == cudaSuccess && r1 > r0)
+      e = cudaMemcpyAsync(static_cast<char*>(dst) + r0 * row_bytes, static_cast<const char*>(src) + r0 * row_bytes,
+                          (r1 - r0) * row_bytes, kind, cs[c]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[c], cs[c]);
+  }
+  for (int c = 0; c < kCopyStreams && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(s, ev[c], 0);
+  return e;
+}
+
+}  // namespace apsp
+
 extern "C" apsp_status apsp_fw_host(const float* W, float* D, int32_t* P, int n, const apsp_options* opt,
                                     apsp_run_info* info, void* stream) {
   if (n < 1 || !W || !D || !P) return APSP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)n * n * sizeof(float);
+  cudaStream_t* cs = nullptr;
+  if (copy_streams(&cs) != cudaSuccess) return APSP_ECUDA;
+  cudaEvent_t ev[kCopyStreams + 1] = {};
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return APSP_ECUDA;
+    }
   // W goes straight into the device D and the solve runs in place (W may alias D).
   float* dD = nullptr;
   int32_t* dP = nullptr;
+  apsp_status st = APSP_OK;
   if (cudaMallocAsync(&dD, bytes, s) != cudaSuccess || cudaMallocAsync(&dP, bytes, s) != cudaSuccess) {
     cudaGetLastError();
-    if (dD) cudaFreeAsync(dD, s);
-    cudaStreamSynchronize(s);
-    return APSP_ENOMEM;
+    st = APSP_ENOMEM;
   }
-  apsp_status st = APSP_OK;
-  if (cudaMemcpyAsync(dD, W, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) st = APSP_ECUDA;
+  const size_t row = (size_t)n * sizeof(float);
+  if (st == APSP_OK && chunked_copy(dD, W, n, row, cudaMemcpyHostToDevice, s, cs, ev) != cudaSuccess) st = APSP_ECUDA;
   if (st == APSP_OK) st = fw_run(dD, dD, dP, n, opt, nullptr, 0, info, s);
   if (st == APSP_OK) {
-    if (cudaMemcpyAsync(D, dD, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(P, dP, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (chunked_copy(D, dD, n, row, cudaMemcpyDeviceToHost, s, cs, ev) != cudaSuccess ||
+        chunked_copy(P, dP, n, row, cudaMemcpyDeviceToHost, s, cs, ev) != cudaSuccess)
       st = APSP_ECUDA;
   }
-  cudaFreeAsync(dD, s);
-  cudaFreeAsync(dP, s);
+  if (dD) cudaFreeAsync(dD, s);
+  if (dP) cudaFreeAsync(dP, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st == APSP_OK) st = APSP_ECUDA;
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st == APSP_ENOMEM) return st;
   if (st == APSP_OK) st = apsp_device_status(1);
   return st;
 }

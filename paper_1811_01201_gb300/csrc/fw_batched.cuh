@@ -12,24 +12,28 @@
 //    thread updates its two elements only on strict improvement, so row k and
 //    column k (which cannot improve at step k because D[k][k] = 0) are never
 //    written during step k.
-//  * phase 2: one warp per line -- a column of the row panel or a row of the
-//    column panel. Lane t holds element t of the line and the matching row
-//    (or column) of the diagonal tile in registers; step k broadcasts the
-//    line's element k with a shuffle, and each lane applies the strict-'<'
-//    update with its path entry. The finished lines are written to global
-//    memory and into the shared panels phase 3 reads.
-//  * phase 3: every element outside row/column band r relaxes through the 32
-//    panel entries (no barriers: the panels are fixed). Keyed graphs use
-//    TR x 128 tiles (TR = 128, 64 or 32, chosen per graph by the host's
-//    autotuner), others 4x4 elements per thread per 64x128 tile.
+//  * phase 2: the lines of the row and column panels (a column of the row
+//    panel, a row of the column panel): one thread per line on exact keys, or
+//    one warp per line with a shuffle per step. The finished lines go to
+//    global memory and into the shared panels phase 3 reads.
+//  * phase 3: every element outside row and column band r relaxes through the
+//    32 panel entries (no barriers: the panels are fixed). It runs over the
+//    compressed index space of the m = n - kw rows and columns outside the
+//    band (the panels are stored in that space), so the band and the padding
+//    of a tile grid over n cost nothing; the panels hold k pairs, so one
+//    add.rn.f32x2 forms two candidates and one three-input min takes both.
+//    Tiles are 32 x 64, 64 x 64 or 128 x 64 (chosen per graph by the host's
+//    size rule or autotuner); the next tile's elements load while the current
+//    one computes.
 //
-// Exact P at one FADD + FMNMX per phase-3 update: for graphs whose weights are
-// all integers and whose longest possible path keeps every key below 2^24,
-// phase 3 runs on keys M*d + slot (M = 64): the column panel carries slot
-// k+1, the old value slot 0. min over keys then reproduces the strict-'<'
-// sweep exactly (the old value wins ties; among equal new values the smallest
-// k). Other graphs use a warp-cooperative first-k search for the improved
-// elements of phase 3.
+// Exact P at one add and one min per update (as on the single-graph path):
+// for graphs whose weights are all integers and whose longest possible path
+// keeps every key below 2^24, phase 3 runs on keys 2^23 + M*d + slot (M = 64):
+// the column panel carries slot k+1, the old value slot 0. min over keys then
+// reproduces the strict-'<' sweep exactly (the old value wins ties; among
+// equal new values the smallest k), and the key's bits hold the slot and the
+// value. Other graphs compare with the old values and search the first k of
+// each improved element, one k per lane of a warp.
 #pragma once
 
 #include "fw_common.cuh"
@@ -46,7 +50,7 @@ struct BatchGraph {
   float* D;
   int32_t* P;
   int n;
-  int ph3_rows;  // phase-3 tile height on keyed graphs: 128, 64 or 32 (0 = 128); set by the autotuner
+  int ph3_rows;  // phase-3 tile of keyed graphs by its height: 32 (32 x 64), 64 (64 x 64), 128 (128 x 64)
 };
 
 struct BatchQueue {
@@ -54,11 +58,15 @@ struct BatchQueue {
   unsigned int done;     // graphs finished
 };
 
-// Shared-memory layout (floats): diag[32][33], gR[32][36], gC[32][36], As[32][ldp], Bs[32][ldp]
+// Shared-memory layout (floats): diag[32][33], gR[32][36], gC[32][36], then the
+// two panels as k pairs in the compressed index space: As2[16][SP] with
+// As2[kp*SP + 2*i' + e] = A[i][2kp + e] and Bs2[16][SP] with
+// Bs2[kp*SP + 2*j' + e] = B[2kp + e][j] (i', j' = row / column index with the
+// band taken out). SP covers a whole grid of the largest tile.
 constexpr int kBG = 36;  // row stride of the key-form diagonal copies (16-byte aligned rows)
-__host__ __device__ constexpr int batched_ldp(int n_max) { return ((n_max + 31) / 32) * 32 + 8; }
+__host__ __device__ constexpr int batched_sp(int n_max) { return 2 * (((n_max + 127) / 128) * 128) + 8; }
 __host__ __device__ constexpr size_t batched_smem_bytes(int n_max) {
-  return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * kBG + 2 * (size_t)32 * batched_ldp(n_max)) + 64;
+  return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * kBG + 2 * (size_t)(kBBS / 2) * batched_sp(n_max)) + 64;
 }
 
 __device__ __forceinline__ float floor_small(float v) {
@@ -71,15 +79,146 @@ __device__ __forceinline__ float key_floor(float key) {
   return floor_small(key * (1.f / kBKeyM)) * kBKeyM;
 }
 
-// Phase-3 tile of keyed graphs: TR rows x 128 columns, 16 x 32 threads with
-// TR/16 x 4 elements each (TR = 128, 64 or 32).
-template <bool KEYED, int TR>
-__device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, int ldp) {
+constexpr float kBOff = 8388608.f;  // 2^23: phase-3 keys lie in [2^23, 2^24)
+
+__device__ __forceinline__ float2 bfadd2(float2 a, float2 b) {
+  // two independent IEEE round-to-nearest fp32 additions in one instruction
+  unsigned long long pa, pb, pc;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(pa) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(pb) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(pc) : "l"(pa), "l"(pb));
+  float2 c;
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(pc));
+  return c;
+}
+
+// Phase 3 of one round over the compressed m x m index space. Threads as 32
+// (ty) x 16 (tx); a thread owns rows tr*32*RA + ty*RA + a (a < RA) and columns
+// tc*16*RC + 32*q + 2*tx + e (q < RC/2, e < 2), so each 128-bit B load of a
+// half warp covers 256 contiguous bytes and each A load is a broadcast.
+template <bool KEYED, int RA, int RC>
+__device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* __restrict__ P, int n, int kb, int kw,
+                                               const float* As2, const float* Bs2, int SP) {
+  constexpr int TH = 32 * RA, TW = 16 * RC, NQ = RC / 2;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, lane = tid & 31;
+  const float INF = f32_inf();
+  const int m = n - kw;
+  const int tiles_c = (m + TW - 1) / TW;
+  const int ntile = ((m + TH - 1) / TH) * tiles_c;
+  auto row_of = [&](int tile, int a) { return (tile / tiles_c) * TH + ty * RA + a; };
+  auto col_of = [&](int tile, int q, int e) { return (tile % tiles_c) * TW + 32 * q + 2 * tx + e; };
+  auto actual = [&](int x) { return x + (x >= kb ? kw : 0); };
+  float nxt[RA][RC];
+  auto load_tile = [&](int tile) {
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int ic = row_of(tile, a);
+      const size_t rowoff = (size_t)actual(ic) * n;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int jc = col_of(tile, q, e);
+          nxt[a][2 * q + e] = (ic < m && jc < m) ? D[rowoff + actual(jc)] : INF;
+        }
+    }
+  };
+  if (ntile > 0) load_tile(0);
+  for (int tile = 0; tile < ntile; ++tile) {
+    float d[RA][RC], old[RA][RC];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        old[a][c] = nxt[a][c];
+        d[a][c] = KEYED ? __fmaf_rn(nxt[a][c], kBKeyM, kBOff) : nxt[a][c];  // slot 0; INF stays INF
+      }
+    if (tile + 1 < ntile) load_tile(tile + 1);
+    const float* Ap = As2 + 2 * row_of(tile, 0);
+    const float* Bp = Bs2 + 2 * col_of(tile, 0, 0);
+#pragma unroll 4
+    for (int kp = 0; kp < kBBS / 2; ++kp) {
+      float2 av[RA], bv[RC];
+      if constexpr (RA == 1) {
+        av[0] = *reinterpret_cast<const float2*>(Ap + kp * SP);
+      } else {
+#pragma unroll
+        for (int h = 0; h < RA / 2; ++h) {
+          const float4 x = *reinterpret_cast<const float4*>(Ap + kp * SP + 4 * h);
+          av[2 * h] = make_float2(x.x, x.y);
+          av[2 * h + 1] = make_float2(x.z, x.w);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 y = *reinterpret_cast<const float4*>(Bp + kp * SP + 64 * q);
+        bv[2 * q] = make_float2(y.x, y.y);
+        bv[2 * q + 1] = make_float2(y.z, y.w);
+      }
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+          const float2 s2 = bfadd2(av[a], bv[c]);
+          d[a][c] = fminf(fminf(d[a][c], s2.x), s2.y);
+        }
+    }
+    uint32_t imp = 0;  // non-keyed: improved elements, bit a*RC + c
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int ic = row_of(tile, a);
+      if (ic >= m) continue;
+      const size_t rowoff = (size_t)actual(ic) * n;
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        const int jc = col_of(tile, c >> 1, c & 1);
+        if (jc >= m) continue;
+        if (KEYED) {
+          // keys in [2^23, 2^24): bits 0x4B000000 | (64*v + slot); slot 0 = unchanged
+          const uint32_t bits = __float_as_uint(d[a][c]);
+          const uint32_t sl = bits & 63u;
+          if (sl != 0u) {
+            const size_t off = rowoff + actual(jc);
+            D[off] = __fsub_rn(__uint_as_float(0x4B000000u | ((bits & 0x7FFFFFu) >> 6)), kBOff);
+            P[off] = kb + (int)sl - 1;
+          }
+        } else if (d[a][c] < old[a][c]) {
+          D[rowoff + actual(jc)] = d[a][c];
+          imp |= 1u << (a * RC + c);
+        }
+      }
+    }
+    if (!KEYED && __any_sync(0xffffffffu, imp != 0)) {
+      // first k of each improved element: the warp evaluates its 32 candidates, one k per lane
+#pragma unroll
+      for (int slot = 0; slot < RA * RC; ++slot) {
+        unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);
+        const float dmine = d[slot / RC][slot % RC];
+        while (bal) {
+          const int src = __ffs(bal) - 1;
+          bal &= bal - 1;
+          const int sty = (tid >> 5) * 2 + (src >> 4), stx = src & 15;  // the owner's (ty, tx)
+          const int ic = (tile / tiles_c) * TH + sty * RA + slot / RC;
+          const int jc = (tile % tiles_c) * TW + 32 * ((slot % RC) >> 1) + 2 * stx + (slot & 1);
+          const float dn = __shfl_sync(0xffffffffu, dmine, src);
+          const int k = lane;
+          const float cand = __fadd_rn(As2[(k >> 1) * SP + 2 * ic + (k & 1)], Bs2[(k >> 1) * SP + 2 * jc + (k & 1)]);
+          const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
+          if (lane == src) P[(size_t)actual(ic) * n + actual(jc)] = kb + __ffs(eq) - 1;
+        }
+      }
+    }
+  }
+}
+
+// One graph, all rounds. Phase-3 tile RA x RC per thread (see batched_phase3).
+template <bool KEYED, int RA, int RC>
+__device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, int SP) {
   float* diag = sm;                 // [32][33]
   float* gR = sm + 32 * 33;         // gR[k * kBG + i] = M * diag[i][k] + k + 1   (key form, row-panel lines)
   float* gC = gR + 32 * kBG;        // gC[k * kBG + j] = M * diag[k][j] + k + 1   (key form, column-panel lines)
-  float* As = gC + 32 * kBG;        // As[k * ldp + i] = D[i][kb + k]   (column panel, transposed)
-  float* Bs = As + 32 * ldp;        // Bs[k * ldp + j] = D[kb + k][j]   (row panel)
+  float* As2 = gC + 32 * kBG;       // column panel A[i][kb + k], k pairs, compressed rows
+  float* Bs2 = As2 + (kBBS / 2) * SP;  // row panel B[kb + k][j], k pairs, compressed columns
   const int n = g.n;
   float* __restrict__ D = g.D;
   int32_t* __restrict__ P = g.P;
@@ -87,6 +226,8 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
   constexpr int NW = kBThreads / 32;
   const float INF = f32_inf();
   const int R = (n + kBBS - 1) / kBBS;
+  // panel entry (k, compressed line lc) in the k-pair layout
+  auto pidx = [SP](int k, int lc) { return (k >> 1) * SP + 2 * lc + (k & 1); };
 
   for (int r = 0; r < R; ++r) {
     const int kb = r * kBBS;
@@ -117,19 +258,9 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
         if (p1 >= 0 && j0 + 1 < kw) { D[(size_t)(kb + i) * n + kb + j0 + 1] = diag[i * 33 + j0 + 1]; P[(size_t)(kb + i) * n + kb + j0 + 1] = p1; }
       }
     }
-    // diagonal block entries of the panels (rows/cols in band r); in key form
-    // the column panel carries slot k+1 and both are scaled by M
-    for (int t = tid; t < 32 * 32; t += kBThreads) {
-      const int k = t >> 5, x = t & 31;
-      if (x < kw) {
-        const float av = diag[x * 33 + k];  // D[kb+x][kb+k]
-        const float bv = diag[k * 33 + x];  // D[kb+k][kb+x]
-        As[k * ldp + kb + x] = KEYED ? fmaf(av, kBKeyM, (float)(k + 1)) : av;
-        Bs[k * ldp + kb + x] = KEYED ? bv * kBKeyM : bv;
-      }
-    }
 
     // ---------------- phase 2: lines of the row and column panels
+    const int nl = n - kw;  // lines per panel (= the compressed size m of phase 3)
     if (KEYED) {
       // key-form copies of the diagonal tile, then one thread per line with the
       // line's 32 keys in registers: step k adds the line's own value part at k
@@ -139,14 +270,13 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
         gC[k * kBG + x] = fmaf(diag[k * 33 + x], kBKeyM, (float)(k + 1));
       }
       __syncthreads();
-      const int nl = n - kw;
       for (int l = tid; l < 2 * nl; l += kBThreads) {
         const bool rowp = l < nl;  // row-panel column o, else column-panel row o
-        int o = rowp ? l : l - nl;
-        o = o < kb ? o : o + kw;
+        const int lc = rowp ? l : l - nl;
+        const int o = lc < kb ? lc : lc + kw;
         const size_t base = rowp ? (size_t)kb * n + o : (size_t)o * n + kb;
         const size_t stride = rowp ? (size_t)n : 1;
-        const float* g = rowp ? gR : gC;
+        const float* gk = rowp ? gR : gC;
         float x[32];
 #pragma unroll
         for (int t = 0; t < 32; ++t) x[t] = t < kw ? D[base + t * stride] * kBKeyM : INF;
@@ -155,7 +285,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           const float xk = key_floor(x[k]);
 #pragma unroll
           for (int t = 0; t < 32; t += 4) {
-            const float4 g4 = *reinterpret_cast<const float4*>(g + k * kBG + t);
+            const float4 g4 = *reinterpret_cast<const float4*>(gk + k * kBG + t);
             x[t] = fminf(x[t], __fadd_rn(g4.x, xk));
             x[t + 1] = fminf(x[t + 1], __fadd_rn(g4.y, xk));
             x[t + 2] = fminf(x[t + 2], __fadd_rn(g4.z, xk));
@@ -176,8 +306,9 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
               }
             }
           }
-          if (rowp) Bs[t * ldp + o] = v * kBKeyM;
-          else As[t * ldp + o] = fmaf(v, kBKeyM, (float)(t + 1));
+          // phase-3 operands: B = 64*v, A = 2^23 + 64*v + k + 1 (INF stays INF)
+          if (rowp) Bs2[pidx(t, lc)] = v * kBKeyM;
+          else As2[pidx(t, lc)] = fmaf(v, kBKeyM, kBOff + (float)(t + 1));
         }
       }
     } else {
@@ -188,7 +319,6 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
         drow[k] = diag[lane * 33 + k];
         dcol[k] = diag[k * 33 + lane];
       }
-      const int nl = n - kw;  // lines per panel
       const bool valid = lane < kw;
       // row-panel column o: element t = D[kb+t][o]; c_t = Diag[t][k] + x_k
       for (int l = warp; l < nl; l += NW) {
@@ -202,7 +332,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        Bs[lane * ldp + o] = valid ? x : INF;
+        Bs2[pidx(lane, l)] = valid ? x : INF;
       }
       // column-panel row o: element t = D[o][kb+t]; c_t = x_k + Diag[k][t]
       for (int l = warp; l < nl; l += NW) {
@@ -216,147 +346,13 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
           if (c < x) { x = c; p = kb + k; }
         }
         if (valid && p >= 0) { D[off] = x; P[off] = p; }
-        As[lane * ldp + o] = valid ? x : INF;
+        As2[pidx(lane, l)] = valid ? x : INF;
       }
     }
     __syncthreads();
 
     // ---------------- phase 3: every element outside band r
-    if (R > 1 && KEYED) {
-      // 16 x 32 threads, RA x 4 elements each: TR x 128 tiles; the next tile's
-      // elements are loaded while the current one computes
-      constexpr int RA = TR / 16;
-      const int ty = tid >> 5, tx = lane;
-      const int tiles_r = (n + TR - 1) / TR, tiles_c = (n + 127) / 128;
-      const int ntile = tiles_r * tiles_c;
-      float nxt[RA][4];
-      auto load_tile = [&](int tile) {
-        const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
-        const int i0 = tr * TR + ty * RA, j0 = tc * 128 + tx * 4;
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = i0 + a, j = j0 + c;
-            nxt[a][c] = (i < n && j < n) ? D[(size_t)i * n + j] : INF;
-          }
-      };
-      load_tile(0);
-      for (int tile = 0; tile < ntile; ++tile) {
-        const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
-        const int i0 = tr * TR + ty * RA, j0 = tc * 128 + tx * 4;
-        float d[RA][4];
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) d[a][c] = nxt[a][c] * kBKeyM;
-        if (tile + 1 < ntile) load_tile(tile + 1);
-        if (i0 < n && j0 < n) {
-          const float* Ap = As + i0;
-          const float* Bp = Bs + j0;
-#pragma unroll 8
-          for (int k = 0; k < kBBS; ++k) {
-            float av[RA];
-            if constexpr (RA == 8) {
-              const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
-              const float4 a1 = *reinterpret_cast<const float4*>(Ap + k * ldp + 4);
-              av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
-              av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
-            } else if constexpr (RA == 4) {
-              const float4 a0 = *reinterpret_cast<const float4*>(Ap + k * ldp);
-              av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
-            } else {
-              const float2 a0 = *reinterpret_cast<const float2*>(Ap + k * ldp);
-              av[0] = a0.x; av[1] = a0.y;
-            }
-            const float4 b4 = *reinterpret_cast<const float4*>(Bp + k * ldp);
-            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
-          }
-          // slot 0 = unchanged; slot s = improved at k = s-1
-#pragma unroll
-          for (int a = 0; a < RA; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int i = i0 + a, j = j0 + c;
-              const float key = d[a][c];
-              if (i >= n || j >= n || !(key < INF)) continue;
-              if ((i >= kb && i < kb + kw) || (j >= kb && j < kb + kw)) continue;
-              const float v = floor_small(key * (1.f / kBKeyM));
-              const int sl = (int)__fmaf_rn(-v, kBKeyM, key);
-              if (sl != 0) {
-                D[(size_t)i * n + j] = v;
-                P[(size_t)i * n + j] = kb + sl - 1;
-              }
-            }
-        }
-      }
-    } else if (R > 1) {
-      const int ty = tid >> 5, tx = lane;  // 16 x 32 threads, 4 x 4 elements each: 64 x 128 tile
-      const int tiles_r = (n + 63) / 64, tiles_c = (n + 127) / 128;
-      for (int tile = 0; tile < tiles_r * tiles_c; ++tile) {
-        const int tr = tile / tiles_c, tc = tile - tr * tiles_c;
-        const int i0 = tr * 64 + ty * 4, j0 = tc * 128 + tx * 4;
-        const bool any_row = i0 < n, any_col = j0 < n;
-        float d[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = i0 + a, j = j0 + c;
-            d[a][c] = (i < n && j < n) ? D[(size_t)i * n + j] : INF;
-          }
-        const float old[4][4] = {{d[0][0], d[0][1], d[0][2], d[0][3]}, {d[1][0], d[1][1], d[1][2], d[1][3]},
-                                 {d[2][0], d[2][1], d[2][2], d[2][3]}, {d[3][0], d[3][1], d[3][2], d[3][3]}};
-        if (any_row && any_col) {
-          const float* Ap = As + i0;
-          const float* Bp = Bs + j0;
-#pragma unroll 8
-          for (int k = 0; k < kBBS; ++k) {
-            const float4 a4 = *reinterpret_cast<const float4*>(Ap + k * ldp);
-            const float4 b4 = *reinterpret_cast<const float4*>(Bp + k * ldp);
-            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) d[a][c] = fminf(d[a][c], __fadd_rn(av[a], bv[c]));
-          }
-        }
-        uint32_t imp = 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = i0 + a, j = j0 + c;
-            const bool inside = i < n && j < n && !(i >= kb && i < kb + kw) && !(j >= kb && j < kb + kw);
-            if (inside && d[a][c] < old[a][c]) {
-              D[(size_t)i * n + j] = d[a][c];
-              imp |= 1u << (a * 4 + c);
-            }
-          }
-        if (__any_sync(0xffffffffu, imp != 0)) {
-#pragma unroll
-          for (int slot = 0; slot < 16; ++slot) {
-            unsigned bal = __ballot_sync(0xffffffffu, (imp >> slot) & 1);
-            const float dmine = d[slot >> 2][slot & 3];
-            while (bal) {
-              const int src = __ffs(bal) - 1;
-              bal &= bal - 1;
-              const int li = i0 + (slot >> 2);                 // same ty for the whole warp
-              const int lj = tc * 128 + src * 4 + (slot & 3);
-              const float dn = __shfl_sync(0xffffffffu, dmine, src);
-              const float cand = __fadd_rn(As[lane * ldp + li], Bs[lane * ldp + lj]);
-              const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
-              if (lane == src) P[(size_t)li * n + lj] = kb + __ffs(eq) - 1;
-            }
-          }
-        }
-      }
-    }
+    if (R > 1) batched_phase3<KEYED, RA, RC>(D, P, n, kb, kw, As2, Bs2, SP);
     __syncthreads();  // D and the shared panels are reused by the next round
   }
 }
@@ -365,7 +361,7 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
 // force_rows != 0 overrides every graph's phase-3 tile height (autotuning runs).
 __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGraph* __restrict__ graphs,
                                                                   const int* __restrict__ order, int count,
-                                                                  BatchQueue* q, int ldp, int force_rows) {
+                                                                  BatchQueue* q, int sp, int force_rows) {
   extern __shared__ __align__(16) float smb[];
   __shared__ int s_g, s_keyed;
   __shared__ unsigned s_frac, s_max;
@@ -412,16 +408,16 @@ __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGra
     atomicMax(&s_max, mx);
     __syncthreads();
     if (threadIdx.x == 0) {
-      // keys stay exact while every path length (< n * max_w) plus a panel sum keeps M*(sum) + 32 < 2^24
+      // keys stay exact while 2^23 + M*(a panel sum, at most two path lengths < n * max_w) + 32 < 2^24
       const float mw = __int_as_float((int)s_max);
-      s_keyed = (s_frac == 0) && (2.0f * mw * (float)n <= 262000.0f);
+      s_keyed = (s_frac == 0) && (2.0f * mw * (float)n <= 131000.0f);
     }
     __syncthreads();
     const int rows = force_rows ? force_rows : g.ph3_rows;
-    if (!s_keyed) batched_graph<false, 128>(g, smb, ldp);
-    else if (rows == 32) batched_graph<true, 32>(g, smb, ldp);
-    else if (rows == 64) batched_graph<true, 64>(g, smb, ldp);
-    else batched_graph<true, 128>(g, smb, ldp);
+    if (!s_keyed) batched_graph<false, 2, 4>(g, smb, sp);
+    else if (rows == 32) batched_graph<true, 1, 4>(g, smb, sp);
+    else if (rows == 64) batched_graph<true, 2, 4>(g, smb, sp);
+    else batched_graph<true, 4, 4>(g, smb, sp);
     if (threadIdx.x == 0) atomicAdd(&q->done, 1u);
     __syncthreads();
   }

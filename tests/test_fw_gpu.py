@@ -326,7 +326,14 @@ def test_full_n8192_int_density_half():
 
 @pytest.mark.slow
 def test_full_n32768_int():
-    _sampled_check(32768, 3, 1, 1000, 1.0, "int", bs=64, n_src=4, expect_dtype=apsp.DTYPE_F32)
+    _sampled_check(32768, 3, 1, 1000, 1.0, "int", bs=64, n_src=4, dtype=apsp.DTYPE_F32, expect_dtype=apsp.DTYPE_F32)
+
+
+@pytest.mark.slow
+def test_full_n32768_int_auto_takes_the_16_bit_path():
+    # the same complete graph with dtype AUTO: no distance exceeds its direct edge (<= 1000), so the
+    # exact 16-bit path runs
+    _sampled_check(32768, 3, 1, 1000, 1.0, "int", bs=0, n_src=4, expect_dtype=apsp.DTYPE_U16X2)
 
 
 @pytest.mark.slow
@@ -368,7 +375,7 @@ def test_max_n65536_int_in_place():
     D = inputs.dense_digraph(n, seed, 1, 1000, device=DEV)
     W = D.cpu().numpy()
     P = torch.empty((n, n), dtype=torch.int32, device=DEV)
-    info = apsp.apsp_fw_ex(D, D, P)
+    info = apsp.apsp_fw_ex(D, D, P, dtype=apsp.DTYPE_F32)
     torch.cuda.synchronize()
     assert info.dtype_used == apsp.DTYPE_F32 and info.bs_used == 64
     rng = np.random.default_rng(seed)

@@ -217,5 +217,5 @@ def test_submit_with_options():
             srv.submit(W, flags=apsp.FLAG_TIME_PHASES)
         assert e.value.status == apsp.APSP_EINVAL
         with pytest.raises(apsp.ApspError) as e:
-            srv.submit(inputs.dense_digraph(300, 75, 1, 1000).numpy(), dtype=apsp.DTYPE_U16X2)
+            srv.submit(inputs.dense_digraph(300, 75, 1, 1000, density=0.9).numpy(), dtype=apsp.DTYPE_U16X2)
         assert e.value.status == apsp.APSP_EINVAL
