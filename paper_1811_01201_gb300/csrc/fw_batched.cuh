@@ -63,7 +63,9 @@ struct BatchQueue {
 // As2[kp*SP + 2*i' + e] = A[i][2kp + e] and Bs2[16][SP] with
 // Bs2[kp*SP + 2*j' + e] = B[2kp + e][j] (i', j' = row / column index with the
 // band taken out). SP covers a whole grid of the largest tile.
-constexpr int kBG = 36;  // row stride of the key-form diagonal copies (16-byte aligned rows)
+constexpr int kBG = 36;   // 32 x kBG floats reserved for each key-form diagonal copy
+constexpr int kBG2 = 72;  // its k-pair rows: 16 rows of 64 floats (+ 8 padding), within 32 x kBG
+static_assert(16 * kBG2 <= 32 * kBG, "k-pair diagonal copy exceeds its space");
 __host__ __device__ constexpr int batched_sp(int n_max) { return 2 * (((n_max + 127) / 128) * 128) + 8; }
 __host__ __device__ constexpr size_t batched_smem_bytes(int n_max) {
   return sizeof(float) * ((size_t)32 * 33 + 2 * (size_t)32 * kBG + 2 * (size_t)(kBBS / 2) * batched_sp(n_max)) + 64;
@@ -215,8 +217,8 @@ __device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* _
 template <bool KEYED, int RA, int RC>
 __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, int SP) {
   float* diag = sm;                 // [32][33]
-  float* gR = sm + 32 * 33;         // gR[k * kBG + i] = M * diag[i][k] + k + 1   (key form, row-panel lines)
-  float* gC = gR + 32 * kBG;        // gC[k * kBG + j] = M * diag[k][j] + k + 1   (key form, column-panel lines)
+  float* gR = sm + 32 * 33;         // M * diag[i][k] + k + 1 (key form, row-panel lines), k pairs
+  float* gC = gR + 32 * kBG;        // M * diag[k][j] + k + 1 (key form, column-panel lines), k pairs
   float* As2 = gC + 32 * kBG;       // column panel A[i][kb + k], k pairs, compressed rows
   float* Bs2 = As2 + (kBBS / 2) * SP;  // row panel B[kb + k][j], k pairs, compressed columns
   const int n = g.n;
@@ -262,12 +264,15 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
     // ---------------- phase 2: lines of the row and column panels
     const int nl = n - kw;  // lines per panel (= the compressed size m of phase 3)
     if (KEYED) {
-      // key-form copies of the diagonal tile, then one thread per line with the
-      // line's 32 keys in registers: step k adds the line's own value part at k
+      // key-form copies of the diagonal tile as k pairs (gR[kp*kBG2 + 2x + e] = M*diag[x][k] + k + 1,
+      // gC likewise with diag[k][x], k = 2kp + e), then one thread per line with the line's 32
+      // keys in registers. Steps k and k+1 go together: element k+1 first takes step k's
+      // candidate, then one add.f32x2 forms both steps' candidates of every element and one
+      // three-input min takes them (the same minimum over the same keys as two steps in turn).
       for (int t = tid; t < 32 * 32; t += kBThreads) {
         const int k = t >> 5, x = t & 31;
-        gR[k * kBG + x] = fmaf(diag[x * 33 + k], kBKeyM, (float)(k + 1));
-        gC[k * kBG + x] = fmaf(diag[k * 33 + x], kBKeyM, (float)(k + 1));
+        gR[(k >> 1) * kBG2 + 2 * x + (k & 1)] = fmaf(diag[x * 33 + k], kBKeyM, (float)(k + 1));
+        gC[(k >> 1) * kBG2 + 2 * x + (k & 1)] = fmaf(diag[k * 33 + x], kBKeyM, (float)(k + 1));
       }
       __syncthreads();
       for (int l = tid; l < 2 * nl; l += kBThreads) {
@@ -281,15 +286,18 @@ __device__ __forceinline__ void batched_graph(const BatchGraph& g, float* sm, in
 #pragma unroll
         for (int t = 0; t < 32; ++t) x[t] = t < kw ? D[base + t * stride] * kBKeyM : INF;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float xk = key_floor(x[k]);
+        for (int k = 0; k < 32; k += 2) {
+          const float* gp = gk + (k >> 1) * kBG2;
+          const float xk0 = key_floor(x[k]);
+          x[k + 1] = fminf(x[k + 1], __fadd_rn(gp[2 * (k + 1)], xk0));  // step k on element k+1
+          const float2 xk = make_float2(xk0, key_floor(x[k + 1]));
 #pragma unroll
-          for (int t = 0; t < 32; t += 4) {
-            const float4 g4 = *reinterpret_cast<const float4*>(gk + k * kBG + t);
-            x[t] = fminf(x[t], __fadd_rn(g4.x, xk));
-            x[t + 1] = fminf(x[t + 1], __fadd_rn(g4.y, xk));
-            x[t + 2] = fminf(x[t + 2], __fadd_rn(g4.z, xk));
-            x[t + 3] = fminf(x[t + 3], __fadd_rn(g4.w, xk));
+          for (int t = 0; t < 32; t += 2) {
+            const float4 g4 = *reinterpret_cast<const float4*>(gp + 2 * t);  // (k, k+1) of t and t+1
+            const float2 s0 = bfadd2(make_float2(g4.x, g4.y), xk);
+            const float2 s1 = bfadd2(make_float2(g4.z, g4.w), xk);
+            x[t] = fminf(fminf(x[t], s0.x), s0.y);
+            x[t + 1] = fminf(fminf(x[t + 1], s1.x), s1.y);
           }
         }
 #pragma unroll
