@@ -7,12 +7,11 @@
 // saturating sum min(a + b, 0xFFFF) equals the exact sum whenever it can
 // matter, and D and P come out bit-identical to the fp32 path.
 //
-// The hot loop is one add-min per packed pair of updates: a wrapping add is
-// exact when no a + b can exceed 0xFFFF, which holds when the round's panel
-// maxima (recorded by phases 1-2, INF included) sum to at most 0xFFFF, and
-// then __viaddmin_u16x2 (min(a + b, c) per 16-bit lane) does both in one
-// instruction; otherwise (typically while panels still hold INF) the round
-// uses the saturating form min(d, min(a, ~b) + b) (add.u16x2 + two min.u16x2).
+// The hot loop is PTX add.u16x2 + min.u16x2: two updates per instruction
+// pair. A wrapping add is exact when no a + b can exceed 0xFFFF, which holds
+// when the round's panel maxima (recorded by phases 1-2, INF included) sum to
+// at most 0xFFFF; otherwise (typically while panels still hold INF) the round
+// uses the saturating form sat(a + b) = min(a, ~b) + b (one more min per pair).
 //
 // P comes, as on the fp32 path, from keys where the round allows them: when
 // every panel value of the round is finite and small enough (a + b below
@@ -97,9 +96,10 @@ __device__ __forceinline__ uint32_t umax4(uint4 v) {
 }
 
 // SAT: saturating sums (rounds whose panels may overflow 16 bits); otherwise
-// no sum can exceed 0xFFFF and one add-min instruction (__viaddmin_u16x2: a
-// wrapping add and a min per lane, half rate, three operand reads) does the
-// work of add.u16x2 + min.u16x2 (four operand reads in two issue slots).
+// no sum can exceed 0xFFFF and a wrapping add.u16x2 is exact. Both lanes' add
+// and min run on the ALU pipe, which bounds this loop (a fused
+// __viaddmin_u16x2 measured the same, and a 32-bit integer add, exact here too,
+// measured 8% slower).
 template <int BS, bool SAT>
 __device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint32_t* __restrict__ Ap,
                                                  const uint32_t* __restrict__ Bp) {
@@ -118,7 +118,7 @@ __device__ __forceinline__ void minplus_u16_loop(uint32_t (&w)[8][4], const uint
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (SAT) w[a][q] = vmin16(w[a][q], vadd16(vmin16(av[a], nb[q]), bv[q]));
-        else w[a][q] = __viaddmin_u16x2(av[a], bv[q], w[a][q]);
+        else w[a][q] = vmin16(w[a][q], vadd16(av[a], bv[q]));
       }
   }
 }
