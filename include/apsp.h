@@ -228,18 +228,20 @@ apsp_status apsp_batch_destroy(apsp_batch* b);
  * Autotuner of the batched launch (the paper tunes its block size to the
  * machine, Section 5): phase 3 of a keyed graph runs on tiles of 32 x 64,
  * 64 x 64 or 128 x 64 elements (named by their height: 32, 64, 128), laid
- * over the rows and columns outside the round's block. For each size class
- * the batch holds (n <= 64,
+ * over the rows and columns outside the round's block; by default each graph
+ * takes the shape whose tile grid wastes least for its n (the size rule).
+ * For each size class the batch holds (n <= 64,
  * <= 128, <= 256, <= 512) it times a persistent launch over that class's
- * graphs with each tile height (one warm-up and two timed runs), keeps the
- * fastest, and later apsp_batch_launch calls use it. The block size stays 32
- * (apsp_batched_bs); the tile does not change any result.
- *   rows_out: optional HOST array of 4 ints, the chosen height per class (0
- *             for classes without graphs).
+ * graphs with the size rule and with each tile height for the whole class
+ * (one warm-up and two timed runs each), keeps the fastest, and later
+ * apsp_batch_launch calls use it. The block size stays 32 (apsp_batched_bs);
+ * the tile does not change any result.
+ *   rows_out: optional HOST array of 4 ints, per class the chosen height, 0
+ *             when the size rule was fastest, -1 for classes without graphs.
  * It runs the batch's solves, so W must not alias D (APSP_EINVAL otherwise);
  * it synchronises `stream` and must not run while a launch of b is in flight
- * or during stream capture. Before any autotuning a graph uses height 32 for
- * n <= 96, 64 for n <= 256 and 128 above.
+ * or during stream capture. Before any autotuning every graph uses the size
+ * rule.
  */
 apsp_status apsp_batch_autotune(apsp_batch* b, int* rows_out, void* stream);
 

@@ -318,8 +318,9 @@ class Batch:
         _check(load().apsp_batch_launch(self._h, _stream_ptr(stream)), "apsp_batch_launch")
 
     def autotune(self, stream=None) -> list[int]:
-        """apsp_batch_autotune: time each phase-3 tile height per size class (n <= 64, 128, 256,
-        512) and keep the fastest; returns the chosen heights (0 = no graphs in the class)."""
+        """apsp_batch_autotune: time the per-graph size rule and each phase-3 tile height per size
+        class (n <= 64, 128, 256, 512) and keep the fastest; returns per class the chosen height
+        (0 = the size rule, -1 = no graphs in the class)."""
         rows = (ctypes.c_int * 4)()
         _check(load().apsp_batch_autotune(self._h, rows, _stream_ptr(stream)), "apsp_batch_autotune")
         return [int(x) for x in rows]

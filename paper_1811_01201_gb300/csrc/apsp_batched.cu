@@ -16,9 +16,25 @@
 
 namespace apsp {
 
-// Phase-3 tile of a keyed graph before any autotuning, by its height: 32 (32 x 64 tiles) up to
-// n = 96, 64 (64 x 64) up to n = 256, 128 (128 x 64) above.
-int default_ph3_rows(int n) { return n <= 96 ? 32 : (n <= 256 ? 64 : 128); }
+// Phase-3 tile of a keyed graph before any autotuning, by its height (32: 32 x 64 tiles, 64:
+// 64 x 64, 128: 128 x 64): the shape whose tile grid over the compressed (n - 32) x (n - 32)
+// index space costs least, counting the padded area times the instructions a relaxation takes
+// on that shape (hot loop plus per-tile load and epilogue: 1.78, 1.59 and 1.53).
+int default_ph3_rows(int n) {
+  const long m = std::max(1, n - kBBS);
+  const struct { int rows, cols; double cost; } shapes[3] = {{32, 64, 1.78}, {64, 64, 1.59}, {128, 64, 1.53}};
+  int best = 128;
+  double best_v = 0.0;
+  for (const auto& sh : shapes) {
+    const double v = (double)((m + sh.rows - 1) / sh.rows * sh.rows) * (double)((m + sh.cols - 1) / sh.cols * sh.cols) *
+                     sh.cost;
+    if (best_v == 0.0 || v < best_v) {
+      best_v = v;
+      best = sh.rows;
+    }
+  }
+  return best;
+}
 
 // The batched kernel's shared-memory limit, set once per device (function
 // attributes belong to the device that was current when they were set).
@@ -163,7 +179,8 @@ namespace {
 // Size classes of the phase-3 tile autotuner: n <= 64, <= 128, <= 256, <= 512.
 constexpr int kTuneClasses = 4;
 constexpr int kTuneClassMax[kTuneClasses] = {64, 128, 256, 512};
-constexpr int kTuneRows[3] = {32, 64, 128};
+// Candidates: 0 = each graph's size rule (default_ph3_rows), then one tile for the whole class.
+constexpr int kTuneRows[4] = {0, 32, 64, 128};
 
 int tune_class(int n) {
   for (int c = 0; c < kTuneClasses; ++c)
@@ -185,7 +202,13 @@ extern "C" apsp_status apsp_batch_autotune(apsp_batch* b, int* rows_out, void* s
   if (cudaMalloc(&d_sub, sizeof(int) * b->count) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     st = APSP_ECUDA;
-  int chosen[kTuneClasses] = {0, 0, 0, 0};
+  // the size-rule candidate runs on the table's own tiles: put the rule back first
+  for (BatchGraph& g : b->hg) g.ph3_rows = default_ph3_rows(g.n);
+  if (st == APSP_OK &&
+      cudaMemcpyAsync(b->d_graphs, b->hg.data(), sizeof(BatchGraph) * b->count, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    st = APSP_ECUDA;
+  int chosen[kTuneClasses] = {-1, -1, -1, -1};
   for (int c = 0; c < kTuneClasses && st == APSP_OK; ++c) {
     const std::vector<int>& sub = cls_order[c];
     if (sub.empty()) continue;
@@ -209,14 +232,17 @@ extern "C" apsp_status apsp_batch_autotune(apsp_batch* b, int* rows_out, void* s
         if (rep > 0) t += ms;
       }
       if (st != APSP_OK) break;
-      if (chosen[c] == 0 || t < best) {
+      if (chosen[c] < 0 || t < best) {
         best = t;
         chosen[c] = rows;
       }
     }
   }
   if (st == APSP_OK) {
-    for (BatchGraph& g : b->hg) g.ph3_rows = chosen[tune_class(g.n)];
+    for (BatchGraph& g : b->hg) {
+      const int ch = chosen[tune_class(g.n)];
+      g.ph3_rows = ch > 0 ? ch : default_ph3_rows(g.n);
+    }
     if (cudaMemcpyAsync(b->d_graphs, b->hg.data(), sizeof(BatchGraph) * b->count, cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -109,16 +109,16 @@ def test_autotuned_tiles_give_identical_results():
     Ws, Wd, Dd, Pd = _make(ns, 15, density=0.6)
     b = apsp.Batch(Wd, Dd, Pd)
     rows = b.autotune()
-    assert len(rows) == 4 and all(r in (32, 64, 128) for r in rows)
+    assert len(rows) == 4 and all(r in (0, 32, 64, 128) for r in rows)  # 0: the per-graph size rule
     for Dx in Dd:
         Dx.fill_(-3.0)
     b.launch()
     _check_all(Ws, Dd, Pd)
     b.close()
-    # classes without graphs report 0; in-place batches cannot be autotuned
+    # classes without graphs report -1; in-place batches cannot be autotuned
     Ws, Wd, Dd, Pd = _make([30, 40], 16)
     b = apsp.Batch(Wd, Dd, Pd)
-    assert b.autotune() == [b.autotune()[0], 0, 0, 0] and b.autotune()[0] in (32, 64, 128)
+    assert b.autotune() == [b.autotune()[0], -1, -1, -1] and b.autotune()[0] in (0, 32, 64, 128)
     b.close()
     b = apsp.Batch(Wd, Wd, Pd)
     with pytest.raises(apsp.ApspError) as e:
