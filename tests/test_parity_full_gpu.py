@@ -91,3 +91,12 @@ def test_n32768_int_whole_matrix_and_a_million_walks():
     pairs = random_pairs(n, 1_000_000, 17)
     assert oracle.check_paths(W, D, P, pairs) == 0
     _whole_matrix(W, D, P, bs)
+
+
+@pytest.mark.slow
+def test_u16_benchmark_workload_whole_matrix():
+    # the benchmark's 16-bit workload on which elements improve: n = 16384, U[1,3], half the edges
+    # present (3 * 16383 < 65535), at the library's default block size
+    W, D, P, info = _solve(16384, 9, 1, 3, 0.5, "int", 0, apsp.DTYPE_AUTO)
+    assert info.dtype_used == apsp.DTYPE_U16X2
+    _whole_matrix(W, D, P, info.bs_used)
