@@ -107,27 +107,38 @@ __device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* _
   const int m = n - kw;
   const int tiles_c = (m + TW - 1) / TW;
   const int ntile = ((m + TH - 1) / TH) * tiles_c;
-  auto row_of = [&](int tile, int a) { return (tile / tiles_c) * TH + ty * RA + a; };
-  auto col_of = [&](int tile, int q, int e) { return (tile % tiles_c) * TW + 32 * q + 2 * tx + e; };
   auto actual = [&](int x) { return x + (x >= kb ? kw : 0); };
+  // Tiles in row-major order; tile (tr, tc) covers compressed rows tr*TH + ty*RA + a and columns
+  // tc*TW + 32*q + 2*tx + e. Element offsets fit in 32 bits (n <= 512). For the tile being
+  // prefetched: each row's offset actual(row) * n and each column's actual index, -1 outside.
   float nxt[RA][RC];
-  auto load_tile = [&](int tile) {
+  int nrow[RA], ncol[RC];
+  auto load_tile = [&](int tr_, int tc_) {
 #pragma unroll
     for (int a = 0; a < RA; ++a) {
-      const int ic = row_of(tile, a);
-      const size_t rowoff = (size_t)actual(ic) * n;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int jc = col_of(tile, q, e);
-          nxt[a][2 * q + e] = (ic < m && jc < m) ? D[rowoff + actual(jc)] : INF;
-        }
+      const int ic = tr_ * TH + ty * RA + a;
+      nrow[a] = ic < m ? actual(ic) * n : -1;
     }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      const int jc = tc_ * TW + 32 * (c >> 1) + 2 * tx + (c & 1);
+      ncol[c] = jc < m ? actual(jc) : -1;
+    }
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int c = 0; c < RC; ++c) nxt[a][c] = (nrow[a] >= 0 && ncol[c] >= 0) ? D[nrow[a] + ncol[c]] : INF;
   };
-  if (ntile > 0) load_tile(0);
+  int ntr = 0, ntc = 0;  // the prefetched tile
+  if (ntile > 0) load_tile(0, 0);
   for (int tile = 0; tile < ntile; ++tile) {
+    const int tr = ntr, tc = ntc;
+    int crow[RA], ccol[RC];
     float d[RA][RC], old[RA][RC];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) crow[a] = nrow[a];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) ccol[c] = ncol[c];
 #pragma unroll
     for (int a = 0; a < RA; ++a)
 #pragma unroll
@@ -135,9 +146,13 @@ __device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* _
         old[a][c] = nxt[a][c];
         d[a][c] = KEYED ? __fmaf_rn(nxt[a][c], kBKeyM, kBOff) : nxt[a][c];  // slot 0; INF stays INF
       }
-    if (tile + 1 < ntile) load_tile(tile + 1);
-    const float* Ap = As2 + 2 * row_of(tile, 0);
-    const float* Bp = Bs2 + 2 * col_of(tile, 0, 0);
+    if (++ntc == tiles_c) {
+      ntc = 0;
+      ++ntr;
+    }
+    if (tile + 1 < ntile) load_tile(ntr, ntc);
+    const float* Ap = As2 + 2 * (tr * TH + ty * RA);
+    const float* Bp = Bs2 + 2 * (tc * TW + 2 * tx);
 #pragma unroll 4
     for (int kp = 0; kp < kBBS / 2; ++kp) {
       float2 av[RA], bv[RC];
@@ -168,24 +183,21 @@ __device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* _
     uint32_t imp = 0;  // non-keyed: improved elements, bit a*RC + c
 #pragma unroll
     for (int a = 0; a < RA; ++a) {
-      const int ic = row_of(tile, a);
-      if (ic >= m) continue;
-      const size_t rowoff = (size_t)actual(ic) * n;
+      if (crow[a] < 0) continue;
 #pragma unroll
       for (int c = 0; c < RC; ++c) {
-        const int jc = col_of(tile, c >> 1, c & 1);
-        if (jc >= m) continue;
+        if (ccol[c] < 0) continue;
+        const int off = crow[a] + ccol[c];
         if (KEYED) {
           // keys in [2^23, 2^24): bits 0x4B000000 | (64*v + slot); slot 0 = unchanged
           const uint32_t bits = __float_as_uint(d[a][c]);
           const uint32_t sl = bits & 63u;
           if (sl != 0u) {
-            const size_t off = rowoff + actual(jc);
             D[off] = __fsub_rn(__uint_as_float(0x4B000000u | ((bits & 0x7FFFFFu) >> 6)), kBOff);
             P[off] = kb + (int)sl - 1;
           }
         } else if (d[a][c] < old[a][c]) {
-          D[rowoff + actual(jc)] = d[a][c];
+          D[off] = d[a][c];
           imp |= 1u << (a * RC + c);
         }
       }
@@ -200,13 +212,13 @@ __device__ __forceinline__ void batched_phase3(float* __restrict__ D, int32_t* _
           const int src = __ffs(bal) - 1;
           bal &= bal - 1;
           const int sty = (tid >> 5) * 2 + (src >> 4), stx = src & 15;  // the owner's (ty, tx)
-          const int ic = (tile / tiles_c) * TH + sty * RA + slot / RC;
-          const int jc = (tile % tiles_c) * TW + 32 * ((slot % RC) >> 1) + 2 * stx + (slot & 1);
+          const int ic = tr * TH + sty * RA + slot / RC;
+          const int jc = tc * TW + 32 * ((slot % RC) >> 1) + 2 * stx + (slot & 1);
           const float dn = __shfl_sync(0xffffffffu, dmine, src);
           const int k = lane;
           const float cand = __fadd_rn(As2[(k >> 1) * SP + 2 * ic + (k & 1)], Bs2[(k >> 1) * SP + 2 * jc + (k & 1)]);
           const unsigned eq = __ballot_sync(0xffffffffu, cand == dn);
-          if (lane == src) P[(size_t)actual(ic) * n + actual(jc)] = kb + __ffs(eq) - 1;
+          if (lane == src) P[actual(ic) * n + actual(jc)] = kb + __ffs(eq) - 1;
         }
       }
     }

@@ -173,6 +173,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
     // (always an exact candidate key) gets its value v and P = kb + slot - 1.
     constexpr uint32_t kSlot = (uint32_t)(2 * BS) - 1u;
     constexpr int kSh = KeyParams<BS>::log2M;
+    const uint32_t kCapBits = __float_as_uint(KeyParams<BS>::cap);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int gi = r0 + mp_row(ty, a);
@@ -187,15 +188,26 @@ __device__ __forceinline__ void tile_body(float* __restrict__ D, int32_t* __rest
         if (((kbits[0] | kbits[1] | kbits[2] | kbits[3]) & kSlot) != 0u && !band_r && !band_c) {
           float* dp = D + (size_t)gi * ld + gj;
           int32_t* pp = P + (size_t)gi * ld + gj;
+          // v = (M*v + slot) >> log2(M), rebuilt as the float 2^23 + v minus 2^23 (exact); a clamped
+          // key (a value too large for a key, or INF) does not hold its old value
+          float nv[4];
+          bool clamped = false;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            nv[e] = __fsub_rn(__uint_as_float(0x4B000000u | ((kbits[e] & 0x7FFFFFu) >> kSh)), KeyParams<BS>::off);
+            clamped |= kbits[e] == kCapBits;
+          }
+          if (!clamped) {
+            *reinterpret_cast<float4*>(dp) = make_float4(nv[0], nv[1], nv[2], nv[3]);  // one 16-byte store
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if ((kbits[e] & kSlot) != 0u) dp[e] = nv[e];
+          }
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const uint32_t sl = kbits[e] & kSlot;
-            if (sl != 0u) {
-              // v = (M*v + slot) >> log2(M), rebuilt as the float 2^23 + v minus 2^23 (exact)
-              dp[e] = __fsub_rn(__uint_as_float(0x4B000000u | ((kbits[e] & 0x7FFFFFu) >> kSh)),
-                                KeyParams<BS>::off);
-              pp[e] = kb + (int)sl - 1;
-            }
+            if (sl != 0u) pp[e] = kb + (int)sl - 1;
           }
         }
       }

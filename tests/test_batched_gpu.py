@@ -118,7 +118,10 @@ def test_autotuned_tiles_give_identical_results():
     # classes without graphs report -1; in-place batches cannot be autotuned
     Ws, Wd, Dd, Pd = _make([30, 40], 16)
     b = apsp.Batch(Wd, Dd, Pd)
-    assert b.autotune() == [b.autotune()[0], -1, -1, -1] and b.autotune()[0] in (0, 32, 64, 128)
+    rows = b.autotune()  # the choice follows timings, so a second run may pick another tile
+    assert rows[1:] == [-1, -1, -1] and rows[0] in (0, 32, 64, 128)
+    b.launch()
+    _check_all(Ws, Dd, Pd)
     b.close()
     b = apsp.Batch(Wd, Wd, Pd)
     with pytest.raises(apsp.ApspError) as e:
