@@ -5,10 +5,11 @@
 // footprints stays within the HBM budget and the number of resident jobs
 // within max_slots, then dispatches admitted work onto a pool of CUDA streams
 // as soon as a stream is free:
-//   * graphs of order <= 512 go together into one persistent batched launch
-//     (every graph admitted since the last dispatch joins the next batch), so
-//     requests that arrive while earlier batches run are picked up by the next
-//     one instead of waiting for them to finish;
+//   * graphs of order <= 512 go together into persistent batched launches,
+//     one per size class (n <= 128, <= 256, <= 512; every graph of the class
+//     admitted since the last dispatch joins the next batch), so requests that
+//     arrive while earlier batches run are picked up by the next one instead of
+//     waiting for them to finish, and small ones do not wait for large ones;
 //   * larger graphs run the single-graph blocked path on their own stream.
 // Work on different streams overlaps on the device; the batched launches run on
 // high-priority streams, so that they get SMs while a large solve runs. A host callback at the
@@ -169,6 +170,9 @@ static void CUDART_CB on_dispatch_done(void* arg) {
   s->cv_done.notify_all();
 }
 
+// Size class of a small graph for batching: n <= 128, <= 256, <= 512.
+static int small_class(int n) { return n <= 128 ? 0 : (n <= 256 ? 1 : 2); }
+
 static size_t job_footprint(int n, bool small, int bs, int dtype) {
   const size_t nn = (size_t)n * n;
   size_t f = nn * (sizeof(float) + sizeof(int32_t));
@@ -299,11 +303,15 @@ static void scheduler(ServerImpl* s) {
       d->srv = s;
       d->stream_idx = (int)si;
       if (small_batch) {
+        // one size class per batch, smallest first: every job of a batch completes with its
+        // largest graph, so a small request does not wait for a 512-vertex one
+        int cls = 3;
         for (auto& j : s->admitted)
-          if (j->small) d->jobs.push_back(j);
-        s->admitted.erase(std::remove_if(s->admitted.begin(), s->admitted.end(),
-                                         [](const std::shared_ptr<Job>& j) { return j->small; }),
-                          s->admitted.end());
+          if (j->small) cls = std::min(cls, small_class(j->n));
+        auto in_batch = [cls](const std::shared_ptr<Job>& j) { return j->small && small_class(j->n) == cls; };
+        for (auto& j : s->admitted)
+          if (in_batch(j)) d->jobs.push_back(j);
+        s->admitted.erase(std::remove_if(s->admitted.begin(), s->admitted.end(), in_batch), s->admitted.end());
         const size_t need = d->jobs.size() * (sizeof(BatchGraphDesc) + sizeof(int));
         d->staging = s->pool.get(need, &d->staging_cls);
         if (!d->staging) {
