@@ -186,6 +186,22 @@ def test_dijkstra_and_bellman_ford_vs_scipy():
         np.testing.assert_array_equal(oracle.bellman_ford(W, s), ref[s])
 
 
+@pytest.mark.parametrize("n,density", [(150, 0.3), (300, 1.0)])
+def test_dijkstra_and_bellman_ford_real_weights_vs_scipy(n, density):
+    # real weights U(0,1] (the n=32768 real workload's distribution): the oracle's double
+    # precision Dijkstra checks sampled rows of that solve at 1e-5, so it is pinned on such
+    # graphs too, against scipy's Dijkstra (also double precision) to rounding
+    W = _w(n, 7 + n, 0, 1, density=density, kind="real")
+    G = csg.csgraph_from_dense(W.astype(np.float64), null_value=np.inf)
+    ref = csg.dijkstra(G, directed=True)
+    for s in (0, n // 2, n - 1):
+        got = oracle.dijkstra(W, s)
+        assert (np.isfinite(got) == np.isfinite(ref[s])).all()
+        fin = np.isfinite(got)
+        np.testing.assert_allclose(got[fin], ref[s][fin], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(oracle.bellman_ford(W, s)[fin], ref[s][fin], rtol=1e-12, atol=0)
+
+
 # ---------------------------------------------------------------- structure of P
 
 def _interior(p):
