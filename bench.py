@@ -551,7 +551,8 @@ def run_extra(args, rank: int, world: int):
     with ClockSampler(local) as clk:
         if args.workload == "batched":
             r = run_batched(args, dev)
-            line = {"metric": "APSP graphs/s (4096 graphs, n log-uniform in [16,512])", "value": r["graphs_per_s"],
+            sizes = f"n={args.batch_n}" if args.batch_n > 0 else "n log-uniform in [16,512]"
+            line = {"metric": f"APSP graphs/s ({args.batch_count} graphs, {sizes})", "value": r["graphs_per_s"],
                     "unit": "graphs/s", "gflops": r["gflops"]}
         else:
             r = run_serve(args, dev, args.serve_seconds if args.serve_seconds > 0 else 60.0,
@@ -593,14 +594,16 @@ def run_c2(args, dev, n=8192, seed=2) -> dict:
             "value": round(2.0 * n ** 3 / (ms * 1e-3) / 1e9, 1), "unit": "GFLOPS", "ms_per_step": round(ms, 3)}
 
 
-def run_batched(args, dev, count=4096, seed=6) -> dict:
+def run_batched(args, dev, seed=6) -> dict:
     """4096 independent dense digraphs, n log-uniform in [16, 512], integer weights U[1,100],
-    density 0.7: one CUDA-graph-captured persistent launch vs one library call per graph."""
+    density 0.7: one CUDA-graph-captured persistent launch vs one library call per graph.
+    --batch-n N gives every graph order N (--batch-count graphs), to study one size alone."""
     import torch
 
     import paper_1811_01201_gb300 as apsp
     from paper_1811_01201_gb300 import inputs
-    ns = inputs.batch_sizes(count, seed)
+    count = args.batch_count
+    ns = [args.batch_n] * count if args.batch_n > 0 else inputs.batch_sizes(count, seed)
     Ws = [inputs.dense_digraph(n, inputs.batch_graph_seed(seed, g), 1, 100, density=0.7, device=dev)
           for g, n in enumerate(ns)]
     Ds = [torch.empty_like(w) for w in Ws]
@@ -644,7 +647,8 @@ def run_batched(args, dev, count=4096, seed=6) -> dict:
     s.synchronize()
     t_s = time.perf_counter() - t0
     b.close()
-    return {"workload": f"{count} dense digraphs, n log-uniform [16,512], integer weights U[1,100], density 0.7",
+    sizes = f"n={args.batch_n}" if args.batch_n > 0 else "n log-uniform [16,512]"
+    return {"workload": f"{count} dense digraphs, {sizes}, integer weights U[1,100], density 0.7",
             "ph3_tile_rows_by_class": dict(zip(["n<=64", "n<=128", "n<=256", "n<=512"], rows)),
             "graphs_per_s_size_rule_tiles": round(count / t_default, 1),
             "graphs_per_s": round(count / t_b, 1), "gflops": round(flops / t_b / 1e9, 1),
@@ -774,6 +778,9 @@ def main():
     ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serve"],
                     help="solve: the n=32768 single-graph line (with batched/served extras); "
                          "batched / serve: only that workload, as its own JSON line")
+    ap.add_argument("--batch-count", type=int, default=4096, help="graphs of --workload batched")
+    ap.add_argument("--batch-n", type=int, default=0, help="--workload batched: every graph of this order "
+                    "(0: n log-uniform in [16,512])")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-sweep", action="store_true",
                     help="with --workload serve: also 15 s runs at 50%%, 95%% and 110%% of saturation")
