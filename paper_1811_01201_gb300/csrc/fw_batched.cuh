@@ -399,28 +399,37 @@ __global__ void __launch_bounds__(kBThreads, 1) fw_batched_kernel(const BatchGra
     const int n = g.n;
     // initialise D = W (zero diagonal), P = -1; find integrality and the largest finite weight
     unsigned frac = 0, mx = 0;
-    const size_t nn = (size_t)n * n;
-    constexpr int kInitUnroll = 8;  // loads of a thread in flight together
-    for (size_t t0 = threadIdx.x; t0 < nn; t0 += (size_t)kInitUnroll * kBThreads) {
+    const unsigned nn = (unsigned)n * (unsigned)n;  // n <= kBMaxN: offsets fit in 32 bits
+    constexpr int kInitUnroll = 8;                  // loads of a thread in flight together
+    // (row, column) of the thread's element, advanced by kBThreads elements a step without a
+    // division per element
+    const unsigned step_i = kBThreads / n, step_j = kBThreads - step_i * n;
+    unsigned ri = threadIdx.x / n, rj = threadIdx.x - ri * n;
+    for (unsigned t0 = threadIdx.x; t0 < nn; t0 += kInitUnroll * kBThreads) {
       float w[kInitUnroll];
 #pragma unroll
       for (int u = 0; u < kInitUnroll; ++u) {
-        const size_t t = t0 + (size_t)u * kBThreads;
+        const unsigned t = t0 + u * kBThreads;
         w[u] = t < nn ? g.W[t] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < kInitUnroll; ++u) {
-        const size_t t = t0 + (size_t)u * kBThreads;
+        const unsigned t = t0 + u * kBThreads;
         if (t < nn) {
-          const size_t i = t / n, j = t - i * n;
           float v = w[u];
-          if (i == j) v = 0.f;
+          if (ri == rj) v = 0.f;
           if (v < f32_inf()) {
             frac |= (v != floorf(v));
             mx = max(mx, (unsigned)__float_as_int(v));
           }
           g.D[t] = v;
           g.P[t] = -1;
+        }
+        rj += step_j;
+        ri += step_i;
+        if (rj >= (unsigned)n) {
+          rj -= n;
+          ++ri;
         }
       }
     }
