@@ -78,6 +78,23 @@ def test_f32_keys_near_exactness_bound(bs, scale):
     _expect_exact(W, D, P, bs)
 
 
+@pytest.mark.parametrize("bs", [32, 64, 128])
+@pytest.mark.parametrize("n", [256, 300])
+def test_f32_complete_graph_with_heavy_old_values(bs, n):
+    # light edges around the first 160 vertices make the early rounds keyed while the old values
+    # of the other pairs sit at 32767, whose key 2^23 + 256 * 32767 at BS = 128 is the clamp
+    # value itself (and at n = 300 the working matrix also holds INF padding)
+    W = inputs.dense_digraph(n, seed=70 + bs, lo=1, hi=10)
+    heavy = torch.full((n, n), 32767.0)
+    hub = torch.zeros(n, dtype=torch.bool)
+    hub[:160] = True
+    W = torch.where(hub[:, None] | hub[None, :], W, heavy)
+    W.fill_diagonal_(0.0)
+    D, P, _ = _run(W, bs=bs, dtype=apsp.DTYPE_F32)
+    _expect_exact(W, D, P, bs)
+    assert int((D == 32767.0).sum()) == 0  # every heavy pair found a path through the hub
+
+
 def test_config_n512_dense_int():
     # the small benchmark workload: n=512, integer weights in [1,100], dense
     W = inputs.dense_digraph(512, seed=1, lo=1, hi=100)
